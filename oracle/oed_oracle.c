@@ -1,0 +1,438 @@
+/*
+ * Plain FP64 CPU oracle for the Laplace-approximated expected information gain
+ * (EIG) of Long, Motamed & Tempone, "Fast Bayesian optimal experimental design
+ * for seismic source inversion" (arXiv:1502.07873).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * definition the CUDA path is checked against.  Only the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark may load it.  It shares no code,
+ * header or table with the CUDA library.
+ *
+ * Every routine follows the paper's steps in the paper's order, written out
+ * plainly, with no blocking, fusion or reordering:
+ *   ref_delta_1d       regularised delta / delta' weights   (Sec. 3.3.2, item 2)
+ *   ref_stf            Gaussian source time function          (Sec. 4.1)
+ *   ref_media          Lame parameters from velocities        (Sec. 2.1, c_p, c_s)
+ *   ref_source_patch   f = S(t) M grad(delta)                 (Eq. source, item 2)
+ *   ref_step           one leap-frog step of the FD scheme    (Eqs. interior_disc,
+ *                      absorbing_disc, full_discrete, Full_Disc)
+ *   ref_forward        seismograms g_r(t_m)                   (Eq. forward_model)
+ *   ref_node_hessian   central-FD Jacobian and H_1            (Eq. H1, Eq. H1_numerics,
+ *                      Appendix C)
+ *   ref_scaled_logdet  S = sqrt(diag H_1), S^-T H_1 S^-1      (Sec. 3.3.3)
+ *   ref_dkl            D_KL-hat                               (Thm 4, Eq. DKL_hat)
+ *   ref_eig            sum_i w_i D_KL-hat(theta_i)            (Eqs. intpoly, mcs)
+ *
+ * Readings of points the paper leaves open (the paper cites Nilsson et al. for
+ * A_h and B_h without printing them):
+ *   - grid x_i = i h, depth z_j = j h, j = 0 is the free surface;
+ *   - A_h is the second-order variable-coefficient operator
+ *       (Au)_x = D+x((l+2m) D-x ux) + D+z(m D-z ux) + D0x(l D0z uz) + D0z(m D0x uz)
+ *       (Au)_z = D+x(m D-x uz) + D+z((l+2m) D-z uz) + D0x(m D0z ux) + D0z(l D0x ux)
+ *     with arithmetic-mean half-point coefficients;
+ *   - the free surface j = 0 uses the summation-by-parts closure of that
+ *     operator: A_h is minus the gradient of a discrete strain energy whose
+ *     surface row has quadrature weight 1/2 and a one-sided z-derivative, so
+ *     the traction-free conditions hold naturally and the discrete energy
+ *     cannot grow (a ghost-row closure that applies the interior formula at
+ *     j = 0 has spectral radius above one and is not used);
+ *   - the absorbing rows are first-order Clayton-Engquist, forward in time and
+ *     upwind in space (normal component with c_p, tangential with c_s); the
+ *     leap-frog form with a one-sided B_h is unstable at the boundary node, so
+ *     the forward-Euler upwind form is used; all four corners take the
+ *     left/right rule;
+ *   - S(t) = w/sqrt(2 pi) exp(-w^2 (t - t_s)^2 / 2), i.e. omega_0 = omega_s;
+ *   - delta and delta' have six-point support k-2..k+3.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NT 7
+#define REF_PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------------------
+ * Regularised delta and delta' (Sec. 3.3.2, item 2).  x_k <= x_s < x_{k+1},
+ * alpha = (x_s - x_k)/h.  d[0..5] and dp[0..5] are the weights at nodes
+ * k-2, ..., k+3.
+ * ------------------------------------------------------------------------- */
+void ref_delta_1d(double a, double h, double *d, double *dp)
+{
+    double a2 = a * a, a3 = a2 * a, a4 = a3 * a, a5 = a4 * a, a6 = a5 * a,
+           a7 = a6 * a, a8 = a7 * a, a9 = a8 * a;
+    double P = 5.0 * a5 / 3.0 - 7.0 * a6 / 24.0 - 17.0 * a7 / 12.0 + 9.0 * a8 / 8.0 - a9 / 4.0;
+    double R = -25.0 * a4 / 12.0 - 3.0 * a5 / 4.0 + 59.0 * a6 / 12.0 - 4.0 * a7 + a8;
+
+    d[0] = (a / 12.0 - a2 / 24.0 - a3 / 12.0 - 19.0 * a4 / 24.0 + P) / h;
+    d[1] = (-2.0 * a / 3.0 + 2.0 * a2 / 3.0 + a3 / 6.0 + 4.0 * a4 - 5.0 * P) / h;
+    d[2] = (1.0 - 5.0 * a2 / 4.0 - 97.0 * a4 / 12.0 + 10.0 * P) / h;
+    d[3] = (2.0 * a / 3.0 + 2.0 * a2 / 3.0 - a3 / 6.0 + 49.0 * a4 / 6.0 - 10.0 * P) / h;
+    d[4] = (-a / 12.0 - a2 / 24.0 + a3 / 12.0 - 33.0 * a4 / 8.0 + 5.0 * P) / h;
+    d[5] = (5.0 * a4 / 6.0 - P) / h;
+
+    double h2 = h * h;
+    dp[0] = (-1.0 / 12.0 + a / 12.0 + a2 / 4.0 + 2.0 * a3 / 3.0 + R) / h2;
+    dp[1] = (2.0 / 3.0 - 4.0 * a / 3.0 - a2 / 2.0 - 7.0 * a3 / 2.0 - 5.0 * R) / h2;
+    dp[2] = (5.0 * a / 2.0 + 22.0 * a3 / 3.0 + 10.0 * R) / h2;
+    dp[3] = (-2.0 / 3.0 - 4.0 * a / 3.0 + a2 / 2.0 - 23.0 * a3 / 3.0 - 10.0 * R) / h2;
+    dp[4] = (1.0 / 12.0 + a / 12.0 - a2 / 4.0 + 4.0 * a3 + 5.0 * R) / h2;
+    dp[5] = (-5.0 * a3 / 6.0 - R) / h2;
+}
+
+/* Gaussian source time function of Sec. 4.1 with omega_0 read as omega_s. */
+double ref_stf(double t, double ts, double ws)
+{
+    double s = t - ts;
+    return ws / sqrt(2.0 * REF_PI) * exp(-ws * ws * s * s / 2.0);
+}
+
+/* Node media from a depth-layered model: layer l covers z_top[l] <= z < z_top[l+1];
+ * a node exactly on an interface belongs to the deeper layer.  lambda = rho (vp^2 - 2 vs^2),
+ * mu = rho vs^2 (from c_p = sqrt((lambda + 2 mu)/rho), c_s = sqrt(mu/rho), Sec. 2.1).
+ * Outputs are [nz][nx]. */
+void ref_media(int nx, int nz, double h, int nlayers, const double *z_top, const double *vp,
+               const double *vs, const double *rho, double *lam, double *mu, double *nu)
+{
+    for (int j = 0; j < nz; j++) {
+        double z = j * h;
+        int l = 0;
+        for (int q = 0; q < nlayers; q++)
+            if (z >= z_top[q]) l = q;
+        for (int i = 0; i < nx; i++) {
+            lam[j * nx + i] = rho[l] * (vp[l] * vp[l] - 2.0 * vs[l] * vs[l]);
+            mu[j * nx + i] = rho[l] * vs[l] * vs[l];
+            nu[j * nx + i] = rho[l];
+        }
+    }
+}
+
+/* Spatial part of f = S(t) M grad(delta(x - x_s)) on the 6x6 patch of nodes
+ * (i0 + a, j0 + b), a, b = 0..5:
+ *   f_x = m_xx delta'(x) delta(z) + m_xz delta(x) delta'(z)
+ *   f_z = m_xz delta'(x) delta(z) + m_zz delta(x) delta'(z)
+ * fx[b*6 + a], fz[b*6 + a].  Returns 0, or -1 if the patch leaves the nodes where
+ * the interior formula applies (1 <= i <= nx-2, 0 <= j <= nz-2). */
+int ref_source_patch(const double *theta, int nx, int nz, double h, int *i0, int *j0,
+                     double *fx, double *fz)
+{
+    double xs = theta[0], zs = theta[1];
+    double mxx = theta[4], mxz = theta[5], mzz = theta[6];
+    double qx = xs / h, qz = zs / h;
+    int kx = (int)floor(qx), kz = (int)floor(qz);
+    double dx[6], dpx[6], dz[6], dpz[6];
+    ref_delta_1d(qx - kx, h, dx, dpx);
+    ref_delta_1d(qz - kz, h, dz, dpz);
+    *i0 = kx - 2;
+    *j0 = kz - 2;
+    for (int b = 0; b < 6; b++)
+        for (int a = 0; a < 6; a++) {
+            fx[b * 6 + a] = mxx * dpx[a] * dz[b] + mxz * dx[a] * dpz[b];
+            fz[b * 6 + a] = mxz * dpx[a] * dz[b] + mzz * dx[a] * dpz[b];
+        }
+    if (*i0 < 1 || *i0 + 5 > nx - 2 || *j0 < 0 || *j0 + 5 > nz - 2) return -1;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * One leap-frog step (Eq. Full_Disc):
+ *   interior and free-surface nodes:  u^{m+1} = 2u^m - u^{m-1} + dt^2/nu (A_h u^m + f^m)
+ *   absorbing nodes:                   (u^{m+1} - u^m)/dt = B_h u^m
+ * All fields are [nz][nx]; fx, fz is the full forcing field at t_m (may be NULL).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int nx, nz;
+    double h, dt;
+    const double *lam, *mu, *nu;   /* [nz][nx] */
+} ref_grid;
+
+/* node value of a [nz][nx] array */
+#define AT(a, i, j) ((a)[(size_t)(j) * nx + (i)])
+
+void ref_step(const ref_grid *g, const double *ux, const double *uz, const double *uxm,
+              const double *uzm, const double *fx, const double *fz, double *uxn, double *uzn)
+{
+    int nx = g->nx, nz = g->nz;
+    double h = g->h, dt = g->dt, h2 = h * h;
+    const double *lam = g->lam, *mu = g->mu, *nu = g->nu;
+
+    for (int j = 0; j < nz; j++)
+        for (int i = 0; i < nx; i++) {
+            size_t c = (size_t)j * nx + i;
+            double cp = sqrt((lam[c] + 2.0 * mu[c]) / nu[c]), cs = sqrt(mu[c] / nu[c]);
+            if (i == 0 || i == nx - 1) {
+                /* left / right (all rows, corners included): d_t u = -/+ c d_x u,
+                 * upwind in space, forward in time; normal ux with c_p, tangential uz with c_s */
+                size_t in = (i == 0) ? c + 1 : c - 1;
+                uxn[c] = ux[c] + cp * dt / h * (ux[in] - ux[c]);
+                uzn[c] = uz[c] + cs * dt / h * (uz[in] - uz[c]);
+                continue;
+            }
+            if (j == nz - 1) {
+                /* bottom: normal uz with c_p, tangential ux with c_s */
+                size_t in = c - nx;
+                uxn[c] = ux[c] + cs * dt / h * (ux[in] - ux[c]);
+                uzn[c] = uz[c] + cp * dt / h * (uz[in] - uz[c]);
+                continue;
+            }
+            double pc = AT(lam, i, j) + 2.0 * AT(mu, i, j);
+            double pe = AT(lam, i + 1, j) + 2.0 * AT(mu, i + 1, j);
+            double pw = AT(lam, i - 1, j) + 2.0 * AT(mu, i - 1, j);
+            double ps = AT(lam, i, j + 1) + 2.0 * AT(mu, i, j + 1);
+            double mc = AT(mu, i, j), me = AT(mu, i + 1, j), mw = AT(mu, i - 1, j);
+            double ms = AT(mu, i, j + 1);
+            double le = AT(lam, i + 1, j), lw = AT(lam, i - 1, j), ls = AT(lam, i, j + 1);
+
+            /* D+x((l+2m)_{i-1/2} D-x ux) and D+x(m_{i-1/2} D-x uz): every row */
+            double Ax = (0.5 * (pc + pe) * (AT(ux, i + 1, j) - AT(ux, i, j))
+                       - 0.5 * (pw + pc) * (AT(ux, i, j) - AT(ux, i - 1, j))) / h2;
+            double Az = (0.5 * (mc + me) * (AT(uz, i + 1, j) - AT(uz, i, j))
+                       - 0.5 * (mw + mc) * (AT(uz, i, j) - AT(uz, i - 1, j))) / h2;
+            if (j > 0) {
+                double pn = AT(lam, i, j - 1) + 2.0 * AT(mu, i, j - 1);
+                double mn = AT(mu, i, j - 1), ln = AT(lam, i, j - 1);
+                /* D+z(m_{j-1/2} D-z ux), D+z((l+2m)_{j-1/2} D-z uz) */
+                Ax += (0.5 * (mc + ms) * (AT(ux, i, j + 1) - AT(ux, i, j))
+                     - 0.5 * (mn + mc) * (AT(ux, i, j) - AT(ux, i, j - 1))) / h2;
+                Az += (0.5 * (pc + ps) * (AT(uz, i, j + 1) - AT(uz, i, j))
+                     - 0.5 * (pn + pc) * (AT(uz, i, j) - AT(uz, i, j - 1))) / h2;
+                /* D0x(l D0z uz) + D0z(m D0x uz) */
+                Ax += (le * (AT(uz, i + 1, j + 1) - AT(uz, i + 1, j - 1))
+                     - lw * (AT(uz, i - 1, j + 1) - AT(uz, i - 1, j - 1))) / (4.0 * h2)
+                    + (ms * (AT(uz, i + 1, j + 1) - AT(uz, i - 1, j + 1))
+                     - mn * (AT(uz, i + 1, j - 1) - AT(uz, i - 1, j - 1))) / (4.0 * h2);
+                /* D0x(m D0z ux) + D0z(l D0x ux) */
+                Az += (me * (AT(ux, i + 1, j + 1) - AT(ux, i + 1, j - 1))
+                     - mw * (AT(ux, i - 1, j + 1) - AT(ux, i - 1, j - 1))) / (4.0 * h2)
+                    + (ls * (AT(ux, i + 1, j + 1) - AT(ux, i - 1, j + 1))
+                     - ln * (AT(ux, i + 1, j - 1) - AT(ux, i - 1, j - 1))) / (4.0 * h2);
+            } else {
+                /* free surface j = 0: summation-by-parts closure.  The operator is minus the
+                 * gradient of a discrete strain energy whose surface row carries weight 1/2
+                 * and whose z-derivative is one-sided there (D~z u = (u_1 - u_0)/h); the
+                 * traction-free conditions sigma_xz = sigma_zz = 0 hold naturally.
+                 *   z-edge:   (2/h^2) m_{1/2} (ux_1 - ux_0),  (2/h^2) (l+2m)_{1/2} (uz_1 - uz_0)
+                 *   mixed x:  D0x(l D~z uz) + (m_0 D0x uz_0 + m_1 D0x uz_1)/h
+                 *   mixed z:  D0x(m D~z ux) + (l_0 D0x ux_0 + l_1 D0x ux_1)/h */
+                double l1 = AT(lam, i, 1);
+                Ax += 2.0 * 0.5 * (mc + ms) * (AT(ux, i, 1) - AT(ux, i, 0)) / h2;
+                Az += 2.0 * 0.5 * (pc + ps) * (AT(uz, i, 1) - AT(uz, i, 0)) / h2;
+                double dzuz_e = (AT(uz, i + 1, 1) - AT(uz, i + 1, 0)) / h;
+                double dzuz_w = (AT(uz, i - 1, 1) - AT(uz, i - 1, 0)) / h;
+                double dzux_e = (AT(ux, i + 1, 1) - AT(ux, i + 1, 0)) / h;
+                double dzux_w = (AT(ux, i - 1, 1) - AT(ux, i - 1, 0)) / h;
+                double dxuz0 = (AT(uz, i + 1, 0) - AT(uz, i - 1, 0)) / (2.0 * h);
+                double dxuz1 = (AT(uz, i + 1, 1) - AT(uz, i - 1, 1)) / (2.0 * h);
+                double dxux0 = (AT(ux, i + 1, 0) - AT(ux, i - 1, 0)) / (2.0 * h);
+                double dxux1 = (AT(ux, i + 1, 1) - AT(ux, i - 1, 1)) / (2.0 * h);
+                Ax += (le * dzuz_e - lw * dzuz_w) / (2.0 * h) + (mc * dxuz0 + ms * dxuz1) / h;
+                Az += (me * dzux_e - mw * dzux_w) / (2.0 * h) + (AT(lam, i, 0) * dxux0 + l1 * dxux1) / h;
+            }
+            if (fx) Ax += fx[c];
+            if (fz) Az += fz[c];
+            double r = dt * dt / nu[c];
+            uxn[c] = 2.0 * ux[c] - uxm[c] + r * Ax;
+            uzn[c] = 2.0 * uz[c] - uzm[c] + r * Az;
+        }
+}
+#undef AT
+
+/* ---------------------------------------------------------------------------
+ * Forward solve: zero initial levels u^0 = u^{-1} = 0 (Eq. elastic_2nd), nsteps
+ * leap-frog steps with forcing f^m = S(t_m) f_patch at t_m = m dt, receiver
+ * samples g[m][r][c] = u_c(x_r, t_m) for m = 0..nsteps (Eq. forward_model).
+ * Returns 0, or -1 if the source patch leaves the interior.
+ * ------------------------------------------------------------------------- */
+int ref_forward(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                const double *mu, const double *nu, int nrec, const int *rec_ix,
+                const double *theta, double *g)
+{
+    ref_grid G = {nx, nz, h, dt, lam, mu, nu};
+    int i0, j0;
+    double px[36], pz[36];
+    if (ref_source_patch(theta, nx, nz, h, &i0, &j0, px, pz) != 0) return -1;
+    size_t n = (size_t)nx * nz;
+    double *ux = calloc(n, sizeof(double)), *uz = calloc(n, sizeof(double));
+    double *uxm = calloc(n, sizeof(double)), *uzm = calloc(n, sizeof(double));
+    double *uxn = calloc(n, sizeof(double)), *uzn = calloc(n, sizeof(double));
+    double *fx = calloc(n, sizeof(double)), *fz = calloc(n, sizeof(double));
+
+    for (int r = 0; r < nrec; r++) {
+        g[(0 * nrec + r) * 2 + 0] = 0.0;
+        g[(0 * nrec + r) * 2 + 1] = 0.0;
+    }
+    for (int m = 0; m < nsteps; m++) {
+        double s = ref_stf(m * dt, theta[2], theta[3]);
+        for (int b = 0; b < 6; b++)
+            for (int a = 0; a < 6; a++) {
+                size_t c = (size_t)(j0 + b) * nx + (i0 + a);
+                fx[c] = s * px[b * 6 + a];
+                fz[c] = s * pz[b * 6 + a];
+            }
+        ref_step(&G, ux, uz, uxm, uzm, fx, fz, uxn, uzn);
+        /* rotate levels: (m-1, m, m+1) -> (m, m+1, free) */
+        double *t;
+        t = uxm; uxm = ux; ux = uxn; uxn = t;
+        t = uzm; uzm = uz; uz = uzn; uzn = t;
+        for (int r = 0; r < nrec; r++) {
+            g[((size_t)(m + 1) * nrec + r) * 2 + 0] = ux[rec_ix[r]];
+            g[((size_t)(m + 1) * nrec + r) * 2 + 1] = uz[rec_ix[r]];
+        }
+    }
+    free(ux); free(uz); free(uxm); free(uzm); free(uxn); free(uzn); free(fx); free(fz);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Gauss-Newton Hessian H_1 at one node from the 2*N_theta central-FD solves
+ * (Eq. H1 with C_eps = sigma^2 I; Eq. H1_numerics; Appendix C):
+ *   J_{m,r,c; j} = (g(theta + d_j e_j) - g(theta - d_j e_j)) / (2 d_j),
+ *   d_j = rel_step (hi_j - lo_j),
+ *   H_rec[r][w] = sigma^-2 sum_{m < win_levels[w]} sum_c J_{m,r,c}^T J_{m,r,c}
+ *   H = sigma^-2 sum_{m <= nsteps} sum_r sum_c J^T J.
+ * H_rec ([nrec][nwin][49]) may be NULL.  Returns 0 or -1 (source out of range).
+ * ------------------------------------------------------------------------- */
+int ref_node_hessian(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                     const double *mu, const double *nu, int nrec, const int *rec_ix,
+                     const double *theta, const double *lo, const double *hi, double rel_step,
+                     double sigma, int nwin, const int *win_levels, double *H, double *H_rec)
+{
+    size_t nrow = (size_t)(nsteps + 1) * nrec * 2;
+    double *gp = malloc(sizeof(double) * nrow), *gm = malloc(sizeof(double) * nrow);
+    double *J = malloc(sizeof(double) * nrow * NT);
+    int rc = 0;
+    for (int j = 0; j < NT && rc == 0; j++) {
+        double d = rel_step * (hi[j] - lo[j]);
+        double tp[NT], tm[NT];
+        for (int q = 0; q < NT; q++) tp[q] = tm[q] = theta[q];
+        tp[j] += d;
+        tm[j] -= d;
+        rc |= ref_forward(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, tp, gp);
+        rc |= ref_forward(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, tm, gm);
+        for (size_t k = 0; k < nrow; k++) J[k * NT + j] = (gp[k] - gm[k]) / (2.0 * d);
+    }
+    if (rc == 0) {
+        double s2 = 1.0 / (sigma * sigma);
+        for (int a = 0; a < NT * NT; a++) H[a] = 0.0;
+        for (size_t k = 0; k < nrow; k++)
+            for (int a = 0; a < NT; a++)
+                for (int b = 0; b < NT; b++) H[a * NT + b] += s2 * J[k * NT + a] * J[k * NT + b];
+        if (H_rec) {
+            for (int r = 0; r < nrec; r++)
+                for (int w = 0; w < nwin; w++) {
+                    double *Hw = H_rec + ((size_t)r * nwin + w) * NT * NT;
+                    for (int a = 0; a < NT * NT; a++) Hw[a] = 0.0;
+                    for (int m = 0; m < win_levels[w] && m <= nsteps; m++)
+                        for (int c = 0; c < 2; c++) {
+                            const double *row = J + (((size_t)m * nrec + r) * 2 + c) * NT;
+                            for (int a = 0; a < NT; a++)
+                                for (int b = 0; b < NT; b++) Hw[a * NT + b] += s2 * row[a] * row[b];
+                        }
+                }
+        }
+    }
+    free(gp); free(gm); free(J);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------
+ * Scaled log-determinant (Sec. 3.3.3): S = sqrt(diag H), Ht = S^-1 H S^-1,
+ * textbook Cholesky Ht = L L^T, log det H = sum log H_ii + 2 sum log L_ii.
+ * Ht (49 values) is written if non-NULL.  Returns 0, or 1 if H is not
+ * positive definite.
+ * ------------------------------------------------------------------------- */
+int ref_scaled_logdet(const double *H, double *logdet, double *Ht)
+{
+    double S[NT], A[NT * NT], L[NT * NT];
+    for (int i = 0; i < NT; i++) {
+        if (!(H[i * NT + i] > 0.0)) return 1;
+        S[i] = sqrt(H[i * NT + i]);
+    }
+    for (int i = 0; i < NT; i++)
+        for (int j = 0; j < NT; j++) A[i * NT + j] = H[i * NT + j] / (S[i] * S[j]);
+    if (Ht) memcpy(Ht, A, sizeof(A));
+    memset(L, 0, sizeof(L));
+    for (int j = 0; j < NT; j++) {
+        double s = A[j * NT + j];
+        for (int k = 0; k < j; k++) s -= L[j * NT + k] * L[j * NT + k];
+        if (!(s > 0.0)) return 1;
+        L[j * NT + j] = sqrt(s);
+        for (int i = j + 1; i < NT; i++) {
+            double t = A[i * NT + j];
+            for (int k = 0; k < j; k++) t -= L[i * NT + k] * L[j * NT + k];
+            L[i * NT + j] = t / L[j * NT + j];
+        }
+    }
+    double ld = 0.0;
+    for (int i = 0; i < NT; i++) ld += log(H[i * NT + i]) + 2.0 * log(L[i * NT + i]);
+    *logdet = ld;
+    return 0;
+}
+
+/* D_KL-hat (Thm 4, Eq. DKL_hat):
+ *   -1/2 log((2 pi)^n |H^-1|) - n/2 - h(theta*) = 1/2 log det H - n/2 log(2 pi) - n/2 - h,
+ * with h = log of the prior density at theta*. */
+double ref_dkl(double logdet, int n, double log_prior_density)
+{
+    return 0.5 * logdet - 0.5 * n * log(2.0 * REF_PI) - 0.5 * n - log_prior_density;
+}
+
+/* ---------------------------------------------------------------------------
+ * Whole path for one design: for each node i (OpenMP over nodes only),
+ * H_1(theta_i) by ref_node_hessian, log det by ref_scaled_logdet, D_KL-hat by
+ * ref_dkl with the uniform prior density h = -sum_j log(hi_j - lo_j), then
+ * EIG = sum_i w_i D_i over positive-definite nodes, in node order with Kahan
+ * compensation (Eqs. intpoly / mcs).  dkl[i], status[i] (0 ok, 1 not PD,
+ * -1 source out of range) and H[i][49] are written if non-NULL.
+ * nthreads <= 0 keeps the OpenMP default.  Returns the number of threads used.
+ * ------------------------------------------------------------------------- */
+int ref_eig(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+            const double *mu, const double *nu, int nrec, const int *rec_ix, int nnode,
+            const double *theta, const double *w, const double *lo, const double *hi,
+            double rel_step, double sigma, int nthreads, double *eig, double *dkl, int *status,
+            double *Hout)
+{
+    double logprior = 0.0;
+    for (int j = 0; j < NT; j++) logprior -= log(hi[j] - lo[j]);
+    double *D = malloc(sizeof(double) * (nnode > 0 ? nnode : 1));
+    int *st = malloc(sizeof(int) * (nnode > 0 ? nnode : 1));
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < nnode; i++) {
+        double H[NT * NT], ld = 0.0;
+        int rc = ref_node_hessian(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix,
+                                  theta + (size_t)i * NT, lo, hi, rel_step, sigma, 0, NULL, H, NULL);
+        if (rc != 0) {
+            st[i] = -1;
+            D[i] = 0.0;
+            continue;
+        }
+        if (Hout) memcpy(Hout + (size_t)i * NT * NT, H, sizeof(H));
+        st[i] = ref_scaled_logdet(H, &ld, NULL);
+        D[i] = st[i] == 0 ? ref_dkl(ld, NT, logprior) : 0.0;
+    }
+    double sum = 0.0, comp = 0.0;
+    for (int i = 0; i < nnode; i++) {
+        if (st[i] != 0) continue;
+        double y = w[i] * D[i] - comp;
+        double t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    *eig = sum;
+    if (dkl) memcpy(dkl, D, sizeof(double) * nnode);
+    if (status) memcpy(status, st, sizeof(int) * nnode);
+    free(D);
+    free(st);
+    return used;
+}

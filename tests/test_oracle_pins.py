@@ -1,0 +1,470 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a swapped index or a transposed operand) fails at least one of them:
+exact moment conditions of the regularised delta, exactness of the FD operator
+on quadratic fields, exact traction-free behaviour at the surface, the
+absorbing-boundary rates, second-order convergence, linearity in the moment
+tensor, additivity / scaling of H_1, a brute-force determinant, and the
+linear-Gaussian closed form of the expected information gain.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+VP, VS, RHO = 3000.0, 1732.0, 2500.0
+MU = RHO * VS * VS
+LAM = RHO * (VP * VP - 2 * VS * VS)
+P2 = LAM + 2 * MU
+
+
+# ------------------------------------------------------------------ delta (Sec. 3.3.2)
+@pytest.mark.parametrize("alpha", [0.0, 0.13, 0.5, 0.77, 0.999])
+@pytest.mark.parametrize("h", [1.0, 25.0])
+def test_delta_moments_exact(oracle, alpha, h):
+    """Discrete moments: h sum d_j (x_j - x_s)^q = [q = 0], h sum d'_j (x_j - x_s)^q = -[q = 1],
+    q = 0..4 (the defining conditions of the fourth-order regularisation)."""
+    d, dp = oracle.delta_weights(alpha, h)
+    xj = (np.arange(-2, 4) - alpha) * h
+    for q in range(5):
+        m0 = h * np.sum(d * xj ** q)
+        m1 = h * np.sum(dp * xj ** q)
+        assert abs(m0 - (1.0 if q == 0 else 0.0)) < 1e-12 * max(1.0, h ** q)
+        assert abs(m1 - (-1.0 if q == 1 else 0.0)) < 1e-12 * max(1.0, h ** q)
+
+
+def test_delta_continuous_across_cells(oracle):
+    """The weights of cell k at alpha -> 1 equal those of cell k+1 at alpha = 0 shifted by one
+    node, and so do their first two alpha-derivatives (the discretisation is C^2 in x_s)."""
+    eps = 1e-5
+
+    def wts(a):
+        d, dp = oracle.delta_weights(a, 1.0)
+        return np.concatenate([d, [0.0]]), np.concatenate([dp, [0.0]])
+
+    def shifted(a):
+        d, dp = oracle.delta_weights(a, 1.0)
+        return np.concatenate([[0.0], d]), np.concatenate([[0.0], dp])
+
+    for k in range(2):
+        left = wts(1.0)[k]
+        right = shifted(0.0)[k]
+        assert np.allclose(left, right, atol=1e-12)
+        dl = (wts(1.0)[k] - wts(1.0 - eps)[k]) / eps
+        dr = (shifted(eps)[k] - shifted(0.0)[k]) / eps
+        assert np.allclose(dl, dr, atol=1e-3)
+        d2l = (wts(1.0)[k] - 2 * wts(1.0 - eps)[k] + wts(1.0 - 2 * eps)[k]) / eps ** 2
+        d2r = (shifted(2 * eps)[k] - 2 * shifted(eps)[k] + shifted(0.0)[k]) / eps ** 2
+        assert np.allclose(d2l, d2r, atol=2e-1)
+
+
+def test_source_time_function_moments(oracle):
+    """S(t) with omega_0 = omega_s has unit area, mean t_s and variance 1/omega_s^2."""
+    ts, ws = 1.3, 4.5
+    t = np.linspace(ts - 12 / ws, ts + 12 / ws, 200001)
+    s = np.array([oracle.stf(x, ts, ws) for x in t[::10]])
+    tt = t[::10]
+    dt = tt[1] - tt[0]
+    area = np.sum(s) * dt
+    mean = np.sum(s * tt) * dt
+    var = np.sum(s * (tt - ts) ** 2) * dt
+    assert abs(area - 1) < 1e-9
+    assert abs(mean - ts) < 1e-9
+    assert abs(var - 1 / ws ** 2) < 1e-9
+
+
+def test_source_patch_moments(oracle):
+    """First moments of the discrete force density equal minus the moment tensor:
+    sum h^2 f_i (x_k - x_{s,k}) = -M_ik, and the total force vanishes (Eq. source)."""
+    h = 10.0
+    th = np.array([503.7, 311.2, 0.2, 5.0, 2.0e13, -3.0e13, 7.0e13])
+    i0, j0, fx, fz, ok = oracle.source_patch(th, 101, 61, h)
+    assert ok
+    xi = (i0 + np.arange(6)) * h - th[0]
+    zj = (j0 + np.arange(6)) * h - th[1]
+    X, Z = np.meshgrid(xi, zj)   # [b][a]
+    M = {"xx": th[4], "xz": th[5], "zz": th[6]}
+    sc = 1e13
+    assert abs(np.sum(fx) * h * h) / sc < 1e-10
+    assert abs(np.sum(fz) * h * h) / sc < 1e-10
+    assert abs(np.sum(fx * X) * h * h + M["xx"]) / sc < 1e-10
+    assert abs(np.sum(fx * Z) * h * h + M["xz"]) / sc < 1e-10
+    assert abs(np.sum(fz * X) * h * h + M["xz"]) / sc < 1e-10
+    assert abs(np.sum(fz * Z) * h * h + M["zz"]) / sc < 1e-10
+
+
+def test_source_patch_out_of_range_rejected(oracle):
+    th = np.array([5.0, 300.0, 0.2, 5.0, 1e13, 1e13, 1e13])
+    assert not oracle.source_patch(th, 101, 61, 10.0)[4]
+
+
+# ------------------------------------------------------------------ operator A_h, B_h
+def _grid(oracle, nx=13, nz=9, h=7.0, dt=1e-3):
+    return oracle.Grid(nx, nz, h, dt, 1, W.HOMOGENEOUS, [0])
+
+
+def _apply(oracle, G, ux, uz):
+    """A_h u recovered from one step with u^{m-1} = u^m and no forcing."""
+    uxn, uzn = oracle.step(G, ux, uz, ux, uz)
+    return (uxn - ux) * RHO / G.dt ** 2, (uzn - uz) * RHO / G.dt ** 2
+
+
+QUADRATICS = [  # (ux(x, z), uz(x, z), (A u)_x, (A u)_z) of the continuous operator
+    (lambda x, z: x * x, lambda x, z: 0 * x, 2 * P2, 0.0),
+    (lambda x, z: z * z, lambda x, z: 0 * x, 2 * MU, 0.0),
+    (lambda x, z: 0 * x, lambda x, z: x * x, 0.0, 2 * MU),
+    (lambda x, z: 0 * x, lambda x, z: z * z, 0.0, 2 * P2),
+    (lambda x, z: x * z, lambda x, z: 0 * x, 0.0, LAM + MU),
+    (lambda x, z: 0 * x, lambda x, z: x * z, LAM + MU, 0.0),
+]
+
+
+@pytest.mark.parametrize("k", range(len(QUADRATICS)))
+def test_interior_operator_exact_on_quadratics(oracle, k):
+    """A second-order operator reproduces div sigma exactly on quadratic fields; each field
+    isolates one of the eight terms, with its sign and coefficient."""
+    G = _grid(oracle)
+    fx_, fz_, ax, az = QUADRATICS[k]
+    x = np.arange(G.nx) * G.h + 3.0
+    z = np.arange(G.nz) * G.h
+    X, Z = np.meshgrid(x, z)
+    Ax, Az = _apply(oracle, G, fx_(X, Z), fz_(X, Z))
+    sl = (slice(1, G.nz - 1), slice(1, G.nx - 1))
+    scale = abs(P2) * 4
+    assert np.max(np.abs(Ax[sl] - ax)) < 1e-6 * scale
+    assert np.max(np.abs(Az[sl] - az)) < 1e-6 * scale
+
+
+TRACTION_FREE = [  # fields with sigma_xz = sigma_zz = 0 at z = 0 and their div sigma
+    (lambda x, z: z * z, lambda x, z: 0 * x, 2 * MU, 0.0),
+    (lambda x, z: 0 * x, lambda x, z: z * z, 0.0, 2 * P2),
+    (lambda x, z: x * x, lambda x, z: -2 * LAM / P2 * x * z, 2 * P2 - 2 * LAM / P2 * (LAM + MU), 0.0),
+    (lambda x, z: -2 * x * z, lambda x, z: x * x, 0.0, -2 * LAM),
+]
+
+
+@pytest.mark.parametrize("k", range(len(TRACTION_FREE)))
+def test_free_surface_exact_on_traction_free_quadratics(oracle, k):
+    """On the surface row the operator reproduces div sigma exactly for quadratic fields that
+    satisfy the traction-free conditions (Eq. elastic_3rd)."""
+    G = _grid(oracle)
+    fx_, fz_, ax, az = TRACTION_FREE[k]
+    x = np.arange(G.nx) * G.h - 20.0
+    z = np.arange(G.nz) * G.h
+    X, Z = np.meshgrid(x, z)
+    Ax, Az = _apply(oracle, G, fx_(X, Z), fz_(X, Z))
+    scale = abs(P2) * 4
+    assert np.max(np.abs(Ax[0, 1:-1] - ax)) < 1e-6 * scale
+    assert np.max(np.abs(Az[0, 1:-1] - az)) < 1e-6 * scale
+
+
+def test_absorbing_rows_rates(oracle):
+    """First-order Clayton-Engquist rows: d_t u = -c d_n u with c_p for the normal and c_s for
+    the tangential component, outward normal -x, +x (sides) and +z (bottom)."""
+    G = _grid(oracle)
+    x = np.arange(G.nx) * G.h
+    z = np.arange(G.nz) * G.h
+    X, Z = np.meshgrid(x, z)
+    zero = 0 * X
+    for ux, uz in ((X, zero), (zero, X), (Z, zero), (zero, Z)):
+        uxn, uzn = oracle.step(G, ux, uz, ux, uz)
+        rx, rz = (uxn - ux) / G.dt, (uzn - uz) / G.dt
+        gx = 1.0 if ux is X else 0.0
+        gzx = 1.0 if uz is X else 0.0
+        gxz = 1.0 if ux is Z else 0.0
+        gz = 1.0 if uz is Z else 0.0
+        # left column: outward -x, d_t u = +c d_x u; right column: d_t u = -c d_x u
+        assert np.allclose(rx[:, 0], VP * gx, rtol=1e-9, atol=1e-6)
+        assert np.allclose(rz[:, 0], VS * gzx, rtol=1e-9, atol=1e-6)
+        assert np.allclose(rx[:, -1], -VP * gx, rtol=1e-9, atol=1e-6)
+        assert np.allclose(rz[:, -1], -VS * gzx, rtol=1e-9, atol=1e-6)
+        # bottom row (without corners): d_t u = -c d_z u
+        assert np.allclose(rx[-1, 1:-1], -VS * gxz, rtol=1e-9, atol=1e-6)
+        assert np.allclose(rz[-1, 1:-1], -VP * gz, rtol=1e-9, atol=1e-6)
+
+
+def test_scheme_spectral_radius_at_most_one(oracle):
+    """The one-step map of the full scheme (free surface, absorbing sides and bottom, two
+    layers) has spectral radius <= 1: no growing mode."""
+    layers = ((0.0, 2000.0, 1155.0, 2200.0), (150.0, 4500.0, 2598.0, 2700.0))
+    nx, nz, h = 13, 9, 25.0
+    G = oracle.Grid(nx, nz, h, 0.5 * h / 4500.0, 1, layers, [0])
+    n = nx * nz
+    A = np.zeros((4 * n, 4 * n))
+    for k in range(4 * n):
+        v = np.zeros(4 * n)
+        v[k] = 1.0
+        ux, uz, uxm, uzm = (v[i * n:(i + 1) * n].reshape(nz, nx) for i in range(4))
+        a, b = oracle.step(G, ux, uz, uxm, uzm)
+        A[:, k] = np.concatenate([a.ravel(), b.ravel(), ux.ravel(), uz.ravel()])
+    rho = np.max(np.abs(np.linalg.eigvals(A)))
+    assert rho <= 1.0 + 1e-9
+
+
+def test_energy_decays_after_source(oracle):
+    """With the source switched off the wavefield leaves through the absorbing boundaries."""
+    w = W.plain_small()
+    G = oracle.Grid(w.nx, w.nz, w.h, w.dt, 10 * w.nsteps, w.layers, list(range(0, w.nx, 4)))
+    g = oracle.forward(G, [1000.0, 500.0, 0.2, 6.0, 5e13, 3e13, 4e13])
+    env = np.abs(g).reshape(g.shape[0], -1).max(axis=1)
+    peak = env.max()
+    late = env[-w.nsteps:]
+    assert np.all(np.isfinite(env))
+    assert late.max() < 0.2 * peak
+    assert late[-1] <= late[0] * 1.5
+
+
+@pytest.mark.slow
+def test_second_order_convergence(oracle):
+    """Seismograms converge at second order under h -> h/2 (dt proportional to h), at an
+    interior and a surface receiver, for a smooth source away from the boundaries."""
+    th = np.array([3000.0, 1500.0, 0.6, 8.0, 5e13, 2e13, 3e13])
+
+    def rate(rx, rz, T):
+        res = []
+        for h in (100.0, 50.0, 25.0, 12.5):
+            nx, nz = int(6000 / h) + 1, int(3000 / h) + 1
+            dt = 0.5 * h / 3000.0
+            ix = int(round(rx / h)) + int(round(rz / h)) * nx
+            G = oracle.Grid(nx, nz, h, dt, int(round(T / dt)), W.HOMOGENEOUS, [ix])
+            res.append(oracle.forward(G, th)[:: int(round(100 / h))])
+        n = min(len(r) for r in res)
+        e = [np.abs(res[k][:n] - res[k + 1][:n]).max() for k in range(3)]
+        return math.log2(e[1] / e[2])
+
+    assert rate(3600.0, 2100.0, 1.1) > 1.8
+    assert rate(3600.0, 0.0, 1.35) > 1.8
+
+
+def test_mirror_symmetry(oracle):
+    """A source on the mid-line with m_xz = 0: u_x is odd and u_z even about x_s."""
+    nx, nz, h = 41, 21, 50.0
+    xc = (nx - 1) // 2
+    recs = [xc - 12, xc - 5, xc + 5, xc + 12]
+    G = oracle.Grid(nx, nz, h, 0.5 * h / VP, 300, W.HOMOGENEOUS, recs)
+    g = oracle.forward(G, [xc * h, 500.0, 0.2, 6.0, 4e13, 0.0, 7e13])
+    sc = np.abs(g).max()
+    assert np.allclose(g[:, 0, 0], -g[:, 3, 0], atol=1e-11 * sc)
+    assert np.allclose(g[:, 1, 0], -g[:, 2, 0], atol=1e-11 * sc)
+    assert np.allclose(g[:, 0, 1], g[:, 3, 1], atol=1e-11 * sc)
+    assert np.allclose(g[:, 1, 1], g[:, 2, 1], atol=1e-11 * sc)
+
+
+def test_linear_in_moment_tensor(oracle):
+    """g is linear in (m_xx, m_xz, m_zz) (Eq. source)."""
+    w = W.tiny()
+    G = oracle.Grid.from_workload(w)
+    base = [950.0, 470.0, 0.15, 5.5]
+    m = [2e13, -5e13, 8e13]
+    g = oracle.forward(G, base + m)
+    parts = [oracle.forward(G, base + list(np.eye(3)[k])) for k in range(3)]
+    comb_ = sum(m[k] * parts[k] for k in range(3))
+    assert np.max(np.abs(g - comb_)) < 1e-12 * np.max(np.abs(g))
+
+
+# ------------------------------------------------------------------ Jacobian and H_1
+@pytest.fixture(scope="module")
+def tiny_setup(oracle):
+    w = W.tiny(nsteps=120, nrec=4)
+    G = oracle.Grid.from_workload(w)
+    th = np.array([1010.0, 520.0, 0.2, 6.0, 4e13, 2e13, 6e13])
+    H, Hr = oracle.node_hessian(G, th, w.prior_lo, w.prior_hi, w.rel_step, 0.3,
+                                win_levels=[31, 81, w.nlevels])
+    return w, G, th, H, Hr
+
+
+def test_hessian_symmetric_psd(tiny_setup, oracle):
+    w, G, th, H, Hr = tiny_setup
+    assert np.allclose(H, H.T, rtol=1e-14, atol=0)
+    ld, Ht, ok = oracle.scaled_logdet(H)
+    assert ok
+    assert np.all(np.linalg.eigvalsh(Ht) > 0)
+    assert np.allclose(np.diag(Ht), 1.0)
+
+
+def test_hessian_moment_columns_equal_unit_solves(tiny_setup, oracle):
+    """The FD Jacobian columns of m_xx, m_xz, m_zz equal the unit-moment seismograms (the
+    map is linear in M), so H_1's moment block is their Gram matrix over sigma^2."""
+    w, G, th, H, Hr = tiny_setup
+    base = list(th[:4])
+    cols = [oracle.forward(G, base + list(np.eye(3)[k])).ravel() for k in range(3)]
+    gram = np.array([[cols[a] @ cols[b] for b in range(3)] for a in range(3)]) / 0.3 ** 2
+    assert np.allclose(H[4:, 4:], gram, rtol=1e-8)
+
+
+def test_hessian_additive_over_receivers_and_windows(tiny_setup, oracle):
+    """H_1 is a sum over receivers and time levels (Appendix C): the per-receiver full-window
+    blocks add up to H, and a run stopped at level L reproduces the window ending at L."""
+    w, G, th, H, Hr = tiny_setup
+    assert np.allclose(Hr[:, -1].sum(axis=0), H, rtol=1e-12)
+    # receivers split into two runs
+    G1 = oracle.Grid(w.nx, w.nz, w.h, w.dt, w.nsteps, w.layers, w.rec_ix[:2])
+    G2 = oracle.Grid(w.nx, w.nz, w.h, w.dt, w.nsteps, w.layers, w.rec_ix[2:])
+    H1, _ = oracle.node_hessian(G1, th, w.prior_lo, w.prior_hi, w.rel_step, 0.3)
+    H2, _ = oracle.node_hessian(G2, th, w.prior_lo, w.prior_hi, w.rel_step, 0.3)
+    assert np.allclose(H1 + H2, H, rtol=1e-12)
+    # causality: a run of 80 steps equals the window of 81 levels
+    Gs = oracle.Grid(w.nx, w.nz, w.h, w.dt, 80, w.layers, w.rec_ix)
+    Hs, _ = oracle.node_hessian(Gs, th, w.prior_lo, w.prior_hi, w.rel_step, 0.3)
+    assert np.allclose(Hs, Hr[:, 1].sum(axis=0), rtol=1e-12)
+    # monotone in time (Loewner order)
+    assert np.all(np.linalg.eigvalsh(Hr[:, 2].sum(0) - Hr[:, 1].sum(0)) > -1e-9 * np.abs(H).max())
+
+
+def test_hessian_scaling_and_duplicate_receivers(tiny_setup, oracle):
+    w, G, th, H, Hr = tiny_setup
+    H2, _ = oracle.node_hessian(G, th, w.prior_lo, w.prior_hi, w.rel_step, 0.6)
+    assert np.allclose(H2 * 4, H, rtol=1e-12)
+    Gd = oracle.Grid(w.nx, w.nz, w.h, w.dt, w.nsteps, w.layers, list(w.rec_ix) * 2)
+    Hd, _ = oracle.node_hessian(Gd, th, w.prior_lo, w.prior_hi, w.rel_step, 0.3)
+    assert np.allclose(Hd, 2 * H, rtol=1e-12)
+
+
+def test_fd_step_richardson(tiny_setup, oracle):
+    """Central differences are second order in the step: the change of H_1 between steps
+    d, d/2 and d/2, d/4 shrinks by a factor near 4, and is tiny at rel_step = 1e-4."""
+    w, G, th, H, Hr = tiny_setup
+    H2, _ = oracle.node_hessian(G, th, w.prior_lo, w.prior_hi, w.rel_step / 2, 0.3)
+    H4, _ = oracle.node_hessian(G, th, w.prior_lo, w.prior_hi, w.rel_step / 4, 0.3)
+    d = np.sqrt(np.outer(np.diag(H), np.diag(H)))
+    e1 = np.abs(H2 - H) / d
+    e2 = np.abs(H4 - H2) / d
+    k = np.unravel_index(np.argmax(e1), e1.shape)
+    assert e1[k] < 1e-5
+    assert 3.0 < e1[k] / e2[k] < 5.0
+
+
+# ------------------------------------------------------------------ log-det, D_KL, EIG
+def _det_bruteforce(A):
+    """Leibniz expansion over all 7! permutations (no factorisation)."""
+    n = A.shape[0]
+    tot = 0.0
+    for perm in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if perm[i] > perm[j])
+        tot += (-1) ** inv * math.prod(A[i, perm[i]] for i in range(n))
+    return tot
+
+
+def test_scaled_logdet_vs_bruteforce(oracle):
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((7, 7))
+    A = B @ B.T + 0.5 * np.eye(7)
+    s = np.array([1e-3, 1e2, 1.0, 10.0, 1e-14, 3e-14, 1e-13])   # parameter units far apart
+    H = A / np.outer(s, s)
+    ld, Ht, ok = oracle.scaled_logdet(H)
+    assert ok
+    ref = math.log(_det_bruteforce(A)) - 2 * np.sum(np.log(s))
+    assert abs(ld - ref) < 1e-9 * abs(ref)
+
+
+def test_scaled_logdet_flags_not_pd(oracle):
+    H = np.eye(7)
+    H[2, 3] = H[3, 2] = 1.5
+    assert not oracle.scaled_logdet(H)[2]
+    H = np.eye(7)
+    H[5, 5] = 0.0
+    assert not oracle.scaled_logdet(H)[2]
+
+
+def test_dkl_unit_invariance_and_sigma_shift(tiny_setup, oracle):
+    """D_KL-hat with a uniform prior is unchanged when a parameter's unit changes (Sec. 3.3.3
+    scaling), and doubling sigma lowers it by N_theta log 2."""
+    w, G, th, H, Hr = tiny_setup
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+    ld, _, _ = oracle.scaled_logdet(H)
+    d0 = oracle.dkl(ld, 7, oracle.log_uniform_density(lo, hi))
+    c = np.array([1e-3, 1.0, 1e3, 1.0, 1e-13, 1.0, 1.0])   # metres->km, s->ms, N m -> 1e13 N m
+    Hc = H / np.outer(c, c)
+    ldc, _, _ = oracle.scaled_logdet(Hc)
+    d1 = oracle.dkl(ldc, 7, oracle.log_uniform_density(lo * c, hi * c))
+    assert abs(d1 - d0) < 1e-9 * abs(d0)
+    ld2, _, _ = oracle.scaled_logdet(H / 4)
+    d2 = oracle.dkl(ld2, 7, oracle.log_uniform_density(lo, hi))
+    assert abs((d0 - d2) - 7 * math.log(2)) < 1e-9
+
+
+def test_linear_gaussian_closed_form(oracle):
+    """For g(theta) = A theta with Gaussian prior N(0, P) and noise sigma^2 I the exact EIG is
+    1/2 log det(I + P A^T A / sigma^2).  The Laplace estimate of Thm 4 (D_KL-hat averaged over
+    the prior, with the Gaussian log-density as h) approaches it with error O(1/N)."""
+    rng = np.random.default_rng(3)
+    n = 7
+    P = np.diag(rng.uniform(0.5, 2.0, n))
+    Pinv = np.linalg.inv(P)
+    gaps = []
+    for N in (200, 800, 3200):
+        A = rng.standard_normal((N, n))
+        sigma = 1.0
+        H = A.T @ A / sigma ** 2
+        ld, _, ok = oracle.scaled_logdet(H)
+        assert ok
+        thetas = rng.multivariate_normal(np.zeros(n), P, size=400)
+        logp = [-0.5 * (n * math.log(2 * math.pi) + math.log(np.linalg.det(P)) + t @ Pinv @ t)
+                for t in thetas]
+        lap = np.mean([oracle.dkl(ld, n, lp) for lp in logp])
+        # the prior log-density averaged exactly: E[-h] = 1/2 log((2 pi e)^n det P)
+        lap_exact_h = oracle.dkl(ld, n, -0.5 * (n * math.log(2 * math.pi * math.e) + math.log(np.linalg.det(P))))
+        exact = 0.5 * np.linalg.slogdet(np.eye(n) + P @ A.T @ A / sigma ** 2)[1]
+        assert abs(lap - lap_exact_h) < 0.1
+        gaps.append(abs(lap_exact_h - exact))
+    assert gaps[0] > gaps[1] > gaps[2]
+    assert gaps[2] < 0.02
+    assert gaps[0] / gaps[2] > 8     # O(1/N): a factor 16 in N gives about 16
+
+
+# ------------------------------------------------------------------ quadrature
+def _golden_counts():
+    rows = []
+    with open(os.path.join(HERE, "golden", "smolyak_counts.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                d, l, c = line.split()[:3]
+                rows.append((int(d), int(l), int(c)))
+    return rows
+
+
+@pytest.mark.parametrize("dim,level,count", _golden_counts())
+def test_smolyak_counts_match_paper(oracle, dim, level, count):
+    x, w = oracle.smolyak(dim, level)
+    assert len(x) == count
+    assert abs(w.sum() - 1.0) < 1e-10
+
+
+def test_smolyak_exact_on_total_degree_monomials(oracle):
+    """Level-L Smolyak Gauss-Legendre integrates total-degree <= 2L+1 polynomials exactly
+    (uniform measure on [-1, 1]^d: E[x^2] = 1/3, E[x^4] = 1/5, E[x^2 y^2] = 1/9)."""
+    x, w = oracle.smolyak(7, 3)
+    assert np.sum(w) == pytest.approx(1.0, abs=1e-12)
+    assert np.sum(w * x[:, 0] ** 2) == pytest.approx(1 / 3, abs=1e-12)
+    assert np.sum(w * x[:, 3] ** 4) == pytest.approx(1 / 5, abs=1e-12)
+    assert np.sum(w * x[:, 1] ** 2 * x[:, 5] ** 2) == pytest.approx(1 / 9, abs=1e-12)
+    assert np.sum(w * x[:, 2] ** 6) == pytest.approx(1 / 7, abs=1e-12)
+    assert np.sum(w * x[:, 0] ** 3 * x[:, 4]) == pytest.approx(0.0, abs=1e-12)
+    assert (w < 0).sum() == 99
+    assert np.abs(w).sum() == pytest.approx(377.0, rel=1e-9)
+
+
+def test_monte_carlo_nodes(oracle):
+    w = W.plain_small()
+    th, wt = oracle.mc_nodes(w.uniforms(), w.prior_lo, w.prior_hi)
+    assert th.shape == (16, 7) and np.allclose(wt, 1 / 16)
+    assert np.all(th >= np.array(w.prior_lo)) and np.all(th <= np.array(w.prior_hi))
+
+
+def test_small_workload_scaled_hessian_conditioning(oracle):
+    """Sec. 4.2: scaling by sqrt(diag H_1) brings cond from ~1e30 to O(10) (the paper prints
+    3.88e30 and 12.16 for its own workload)."""
+    w = W.plain_small()
+    G = oracle.Grid.from_workload(w)
+    th = (np.array(w.prior_lo) + np.array(w.prior_hi)) / 2
+    H, _ = oracle.node_hessian(G, th, w.prior_lo, w.prior_hi, w.rel_step, 0.4)
+    _, Ht, ok = oracle.scaled_logdet(H)
+    assert ok
+    assert np.linalg.cond(H) > 1e25
+    assert 1.0 < np.linalg.cond(Ht) < 1e3
