@@ -161,20 +161,20 @@ void ref_step(const ref_grid *g, const double *ux, const double *uz, const doubl
     for (int j = 0; j < nz; j++)
         for (int i = 0; i < nx; i++) {
             size_t c = (size_t)j * nx + i;
-            double cp = sqrt((lam[c] + 2.0 * mu[c]) / nu[c]), cs = sqrt(mu[c] / nu[c]);
-            if (i == 0 || i == nx - 1) {
+            if (i == 0 || i == nx - 1 || j == nz - 1) {
+                double cp = sqrt((lam[c] + 2.0 * mu[c]) / nu[c]), cs = sqrt(mu[c] / nu[c]);
+                if (i == 0 || i == nx - 1) {
                 /* left / right (all rows, corners included): d_t u = -/+ c d_x u,
                  * upwind in space, forward in time; normal ux with c_p, tangential uz with c_s */
-                size_t in = (i == 0) ? c + 1 : c - 1;
-                uxn[c] = ux[c] + cp * dt / h * (ux[in] - ux[c]);
-                uzn[c] = uz[c] + cs * dt / h * (uz[in] - uz[c]);
-                continue;
-            }
-            if (j == nz - 1) {
-                /* bottom: normal uz with c_p, tangential ux with c_s */
-                size_t in = c - nx;
-                uxn[c] = ux[c] + cs * dt / h * (ux[in] - ux[c]);
-                uzn[c] = uz[c] + cp * dt / h * (uz[in] - uz[c]);
+                    size_t in = (i == 0) ? c + 1 : c - 1;
+                    uxn[c] = ux[c] + cp * dt / h * (ux[in] - ux[c]);
+                    uzn[c] = uz[c] + cs * dt / h * (uz[in] - uz[c]);
+                } else {
+                    /* bottom: normal uz with c_p, tangential ux with c_s */
+                    size_t in = c - nx;
+                    uxn[c] = ux[c] + cs * dt / h * (ux[in] - ux[c]);
+                    uzn[c] = uz[c] + cp * dt / h * (uz[in] - uz[c]);
+                }
                 continue;
             }
             double pc = AT(lam, i, j) + 2.0 * AT(mu, i, j);
@@ -300,17 +300,25 @@ int ref_node_hessian(int nx, int nz, double h, double dt, int nsteps, const doub
                      double sigma, int nwin, const int *win_levels, double *H, double *H_rec)
 {
     size_t nrow = (size_t)(nsteps + 1) * nrec * 2;
-    double *gp = malloc(sizeof(double) * nrow), *gm = malloc(sizeof(double) * nrow);
+    double *gall = malloc(sizeof(double) * nrow * 2 * NT);
     double *J = malloc(sizeof(double) * nrow * NT);
     int rc = 0;
+    /* the 2 N_theta perturbed solves are independent (run in parallel when this is
+     * not already inside a parallel region) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : rc) if (!omp_in_parallel())
+#endif
+    for (int q = 0; q < 2 * NT; q++) {
+        int j = q / 2;
+        double d = rel_step * (hi[j] - lo[j]);
+        double t[NT];
+        for (int k = 0; k < NT; k++) t[k] = theta[k];
+        t[j] += (q % 2 == 0) ? d : -d;
+        rc |= ref_forward(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, t, gall + (size_t)q * nrow);
+    }
     for (int j = 0; j < NT && rc == 0; j++) {
         double d = rel_step * (hi[j] - lo[j]);
-        double tp[NT], tm[NT];
-        for (int q = 0; q < NT; q++) tp[q] = tm[q] = theta[q];
-        tp[j] += d;
-        tm[j] -= d;
-        rc |= ref_forward(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, tp, gp);
-        rc |= ref_forward(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, tm, gm);
+        const double *gp = gall + (size_t)(2 * j) * nrow, *gm = gall + (size_t)(2 * j + 1) * nrow;
         for (size_t k = 0; k < nrow; k++) J[k * NT + j] = (gp[k] - gm[k]) / (2.0 * d);
     }
     if (rc == 0) {
@@ -333,7 +341,7 @@ int ref_node_hessian(int nx, int nz, double h, double dt, int nsteps, const doub
                 }
         }
     }
-    free(gp); free(gm); free(J);
+    free(gall); free(J);
     return rc;
 }
 
