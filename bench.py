@@ -1,0 +1,358 @@
+"""Benchmark of the Laplace expected-information-gain hot path on GB300.
+
+One step = one EIG evaluation of the batched workload (401x201 grid, h = 5 m,
+2000 leap-frog steps, 256 Monte Carlo nodes x 15 central-FD solves = 3840
+solves, 20 surface receivers): source setup, all time steps (FP32 stencil),
+FP64 Jacobian / Hessian, FP64 scaled log-determinants and the quadrature sum.
+Inputs are resident in HBM when the timed region starts; the 5.1 GB of
+wavefields per step exceed the 129 MB L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "EIG evals/s & stencil Gcell-upd/s (% HBM roofline) at rel err<=1e-3; p50/p99"
+STENCIL_SRC = os.path.join(ROOT, "paper_1502_07873_gb300", "csrc", "stencil.cu")
+BYTES_PER_CELL_UPDATE = {"f32": 24, "f64": 48}   # read u^m, u^{m-1}; write u^{m+1}; 2 comps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "plain_small"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-nodes", type=int, default=2)
+    ap.add_argument("--nodes", type=int, default=0, help="override the node count (profiling runs)")
+    ap.add_argument("--sigma", type=float, default=0.0, help="use this noise std instead of 1%% of peak")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def stencil_hash() -> str:
+    with open(STENCIL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(workload: str, precision: str):
+    """DRAM bytes per cell-update of the stencil kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel source changed since."""
+    p = os.path.join(ROOT, "profiles", "stencil_dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(precision)
+    if not e or e.get("stencil_sha") != stencil_hash():
+        return None
+    return float(e["dram_bytes_per_cell_update"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(name):
+    return W.batched() if name == "batched" else W.plain_small()
+
+
+def noise_sigma_gpu(P, torch, w, precision):
+    """sigma = 1% of the peak |u| over all surface nodes at the prior-mean source
+    (computed once per grid / medium / duration, outside the timed region)."""
+    prob = P.problem_from_workload(w, precision, rec_ix=list(range(w.nx)))
+    ctx = P.Context(prob, max_solves=15)
+    mean = (np.array(w.prior_lo) + np.array(w.prior_hi)) / 2
+    g = torch.empty((1, w.nlevels, w.nx, 2), dtype=torch.float64, device="cuda")
+    P.oed_forward(ctx, torch.tensor(mean[None], device="cuda"), g)
+    torch.cuda.synchronize()
+    ctx.close()
+    return w.sigma_frac * float(g.abs().max().item())
+
+
+def cpu_baseline(w, sigma, nodes: int):
+    """The FP64 oracle on a bounded sample: `nodes` nodes of the same workload, each
+    node's 14 perturbed solves spread over the host cores."""
+    from oracle import oracle as O
+    O.build()
+    G = O.Grid.from_workload(w)
+    th, wt = O.mc_nodes(w.uniforms(), w.prior_lo, w.prior_hi)
+    lp = O.log_uniform_density(w.prior_lo, w.prior_hi)
+    t0 = time.perf_counter()
+    for i in range(nodes):
+        H, _ = O.node_hessian(G, th[i], w.prior_lo, w.prior_hi, w.rel_step, sigma)
+        ld, _, ok = O.scaled_logdet(H)
+        O.dkl(ld, 7, lp)
+    dt = time.perf_counter() - t0
+    threads = min(14, os.cpu_count() or 1)
+    per_eval = dt / nodes * w.n_nodes
+    return {"value": 1.0 / per_eval, "unit": "EIG evals/s", "cores": int(threads), "kind": "oracle",
+            "sample": f"{nodes} of {w.n_nodes} nodes ({nodes * 14} FP64 solves of "
+                      f"{w.nx}x{w.nz}x{w.nsteps} steps), {dt:.1f} s wall, scaled to one EIG "
+                      f"evaluation"}, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    from oracle import oracle as O
+    O.build()
+    sigma_w = W.batched().sigma_frac
+    mean = (np.array(w.prior_lo) + np.array(w.prior_hi)) / 2
+    Gs = O.Grid(w.nx, w.nz, w.h, w.dt, w.nsteps, w.layers, list(range(w.nx)))
+    sigma = O.noise_sigma(Gs, mean, sigma_w)
+    times = []
+    nodes = max(1, min(args.cpu_sample_nodes, w.n_nodes))
+    for k in range(args.warmup + args.steps):
+        cb, dt = cpu_baseline(w, sigma, nodes)
+        if k >= args.warmup:
+            times.append(dt / nodes * w.n_nodes)
+    per = statistics.mean(times)
+    out = {"impl": "reference", "metric": METRIC, "value": 1.0 / per, "unit": "EIG evals/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "grid": f"{w.nx}x{w.nz}", "time_steps": w.nsteps,
+                      "nodes": w.n_nodes, "solves": 15 * w.n_nodes, "receivers": w.nrec},
+           "cpu_baseline": {**cb, "value": 1.0 / per},
+           "e2e": {"value": 1.0 / per, "unit": "EIG evals/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1502_07873_gb300 as P
+    from paper_1502_07873_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    w = workload(args.workload)
+    if args.nodes:
+        w.n_nodes = args.nodes
+    prec = P.OED_FP32 if args.precision == "f32" else P.OED_FP64
+    sigma = args.sigma if args.sigma > 0 else noise_sigma_gpu(P, torch, w, prec)
+    dev = torch.device("cuda", local)
+    nsolve = 15 * w.n_nodes
+    ctx = P.Context(P.problem_from_workload(w, prec), max_solves=nsolve)
+    # each rank evaluates its own independent batch of nodes (weak scaling)
+    u = w.uniforms(seed=w.seed + 7919 * rank)
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+    theta = torch.tensor(lo + (hi - lo) * u, dtype=torch.float64, device=dev)
+    wt = torch.full((w.n_nodes,), 1.0 / w.n_nodes, dtype=torch.float64, device=dev)
+    H = torch.empty((w.n_nodes, 7, 7), dtype=torch.float64, device=dev)
+    eig = torch.empty(1, dtype=torch.float64, device=dev)
+    nbad = torch.empty(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        P.oed_hessian(ctx, theta, w.prior_lo, w.prior_hi, w.rel_step, sigma, H, stream=stream)
+        P.oed_eig(ctx, H, wt, w.prior_lo, w.prior_hi, eig, n_bad=nbad, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    step_ms, stencil_ms = [], []
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for k in range(args.steps):
+            step()
+            ev[k + 1].record(stream)
+            ev[k + 1].synchronize()
+            ms, launches = ctx.last_step_time()
+            stencil_ms.append(ms / launches)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+    for k in range(args.steps):
+        step_ms.append(ev[k].elapsed_time(ev[k + 1]))
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    eig_val = float(eig.item())
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the host-buffer entry point (pinned inputs, H2D + D2H inside)
+    e2e = None
+    if not args.no_e2e:
+        th_h = theta.cpu().pin_memory()
+        w_h = wt.cpu().pin_memory()
+        P.oed_eig_host(ctx, th_h, w_h, w.prior_lo, w.prior_hi, w.rel_step, sigma)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e_h, _, _ = P.oed_eig_host(ctx, th_h, w_h, w.prior_lo, w.prior_hi, w.rel_step, sigma)
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * args.steps / el, "unit": "EIG evals/s",
+               "h2d_bytes_per_step": int(th_h.numel() * 8 + w_h.numel() * 8),
+               "d2h_bytes_per_step": 8 + 4}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    cells = w.cells * w.nsteps * nsolve
+    per_launch_cells = w.cells * nsolve
+    bpc = BYTES_PER_CELL_UPDATE[args.precision]
+    st_ms = statistics.median(stencil_ms)
+    achieved = per_launch_cells * bpc / (st_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic_bpc = ncu_traffic(w.name, args.precision)
+    value = world * args.steps / (total_ms * 1e-3)
+    cb = None
+    if not args.no_cpu_baseline and world == 1:
+        cb, _ = cpu_baseline(w, sigma, max(1, args.cpu_sample_nodes))
+    lat = sorted(step_ms)
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "EIG evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": w.name, "grid": f"{w.nx}x{w.nz}", "h_m": w.h, "time_steps": w.nsteps,
+                   "nodes_per_gpu": w.n_nodes, "solves_per_gpu": nsolve, "receivers": w.nrec,
+                   "precision": f"{args.precision} stencil; f64 jacobian, hessian, log-det, sum",
+                   "parallelism": f"replicas x{world} (independent node batches)",
+                   "l2": "no flush: 5.1 GB of wavefields per step exceed the 129 MB L2"},
+        "gcell_upd_per_s": world * cells * args.steps / (total_ms * 1e-3) / 1e9,
+        "stencil_gcell_upd_per_s": per_launch_cells / (st_ms * 1e-3) / 1e9,
+        "latency_ms": {"p50": pct(0.5), "p99": pct(0.99)},
+        "eig": eig_val,
+        "sigma": sigma,
+        "roofline": {"bound": "hbm", "kernel": "k_step (leap-frog stencil)", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_cell_update": bpc,
+                     "traffic": (traffic_bpc * per_launch_cells if traffic_bpc else None),
+                     "launch_ms": st_ms},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps * (w.nsteps + 5),
+        "e2e": e2e,
+    }
+    if cb:
+        out["cpu_baseline"] = cb
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

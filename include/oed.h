@@ -1,0 +1,186 @@
+/*
+ * oed.h - C ABI of the GB300 (sm_103a) library for the Laplace-approximated
+ * expected information gain (EIG) of seismic source inversion, after
+ * Long, Motamed & Tempone, "Fast Bayesian optimal experimental design for
+ * seismic source inversion" (arXiv:1502.07873).
+ *
+ * The path: source parameters theta = (x_s, z_s, t_s, omega_s, m_xx, m_xz, m_zz)
+ * (Sec. 2.1, paper order, N_theta = 7) -> 2-D elastic finite-difference forward
+ * solves (Sec. 3.3.1, Eq. Full_Disc) -> receiver seismograms (Eq. forward_model)
+ * -> central finite-difference Jacobian -> Gauss-Newton Hessian
+ * H_1 = sum_{r,m} J^T C_eps^-1 J (Thm 2, Eq. H1; Eq. H1_numerics; Appendix C)
+ * -> scaled log-determinant (Sec. 3.3.3) -> D_KL-hat (Thm 4, Eq. DKL_hat)
+ * -> EIG = sum_i w_i D_KL-hat(theta_i) (Eqs. intpoly and mcs).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int status: OED_OK (0) or one of the OED_E* codes
+ *    below.  oed_last_error() gives a message for the last failure on a context.
+ *  - Array arguments marked "device" are device pointers on the context's
+ *    device (e.g. from torch.empty(..., device="cuda")); "host" arrays are plain
+ *    host memory.  The caller owns every array it passes; the library owns only
+ *    the context and the device workspace it allocates in oed_create().
+ *  - Calls taking a stream enqueue work on that stream (a cudaStream_t passed
+ *    as void*, NULL = legacy default stream) and return before the work ends;
+ *    results are ready once the stream is synchronised.  Calls on one context
+ *    must not overlap (they share its workspace).
+ *  - Grid: nodes x_i = i h (0 <= i < nx), depth z_j = j h (0 <= j < nz); j = 0 is
+ *    the free surface, the two sides and the bottom are absorbing.  The medium is
+ *    piecewise constant in depth.
+ *  - Seismogram layout (time-major): g[solve][m][r][c], m = 0..nsteps time
+ *    levels t_m = m dt, r = receiver, c = 0 (u_x) or 1 (u_z, positive down).
+ */
+#ifndef OED_H
+#define OED_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OED_OK 0
+#define OED_EINVAL 1   /* invalid argument (sizes, pointers, source outside the grid) */
+#define OED_ENOMEM 2   /* device allocation failed, or a request exceeds the workspace */
+#define OED_ENOTPD 3   /* some H_1 is not positive definite (see the per-node status) */
+#define OED_ECUDA 4    /* a CUDA runtime call failed */
+#define OED_ETIMEOUT 5 /* a bounded device wait gave up */
+
+#define OED_FP32 0 /* stencil time stepping in FP32 (Jacobian, H_1, log-det in FP64) */
+#define OED_FP64 1 /* everything in FP64 */
+
+#define OED_NTHETA 7
+#define OED_NH 28 /* unique entries of a symmetric 7x7 matrix, row-major upper triangle */
+
+typedef struct oed_ctx oed_ctx;
+
+/* The discretised problem (Sec. 3.3.1 and Sec. 4.1).  All pointers are host
+ * pointers; the library copies what it needs during oed_create(). */
+typedef struct {
+    int nx, nz;        /* grid nodes along x and depth, nx >= 8, nz >= 8 */
+    double h;          /* grid spacing in metres, > 0 */
+    double dt;         /* time step in seconds, > 0 (CFL: dt <= h / max vp is the
+                          caller's responsibility; the synthetic workloads use 0.5) */
+    int nsteps;        /* leap-frog steps; seismograms hold nsteps + 1 levels */
+    int nlayers;       /* >= 1 layers, piecewise constant in depth */
+    const double *z_top; /* [nlayers] layer tops, z_top[0] = 0, increasing; a node on
+                            an interface belongs to the deeper layer */
+    const double *vp, *vs, *rho; /* [nlayers] P and S speed (m/s), density (kg/m^3) */
+    int nrec;          /* receivers, 1..256 */
+    const int *rec_ix; /* [nrec] surface node index i of each receiver (0 <= i < nx);
+                          repeats allowed */
+    int precision;     /* OED_FP32 or OED_FP64 */
+} oed_problem;
+
+/* Create a context on the current CUDA device with device workspace for up to
+ * max_solves simultaneous forward solves (oed_hessian uses 15 per node and
+ * processes nodes in chunks of max_solves / 15).  Returns OED_ENOMEM if the
+ * workspace does not fit.  *ctx is set to NULL on failure. */
+int oed_create(oed_ctx **ctx, const oed_problem *p, int max_solves);
+
+/* Device bytes oed_create() would allocate for this problem and max_solves
+ * (used for admission by HBM footprint).  Returns 0 for an invalid problem. */
+size_t oed_workspace_bytes(const oed_problem *p, int max_solves);
+
+/* Release the context and its workspace.  NULL is accepted. */
+int oed_destroy(oed_ctx *ctx);
+
+/* Message of the last failing call on ctx (never NULL). */
+const char *oed_last_error(const oed_ctx *ctx);
+
+/* Static name of a status code. */
+const char *oed_status_string(int status);
+
+/* Diagnostics: device time of the stencil launches of the last replayed time
+ * loop (the nsteps leap-frog launches of the last batch of solves run by
+ * oed_forward / oed_hessian on this context), from CUDA events recorded on the
+ * stream that ran them.  Call after that stream has been synchronised.
+ *   ms        host [1] milliseconds
+ *   launches  host [1] or NULL: stencil launches in that interval (0 if none yet) */
+int oed_last_step_time(const oed_ctx *ctx, float *ms, int *launches);
+
+/* Largest node chunk oed_hessian processes per pass (max_solves / 15). */
+int oed_chunk_nodes(const oed_ctx *ctx);
+
+/* Forward map (Eq. forward_model): seismograms of n source vectors.
+ *   theta  device [n][7] FP64, paper order (x_s, z_s, t_s, omega_s, m_xx, m_xz, m_zz)
+ *   g      device [n][nsteps+1][nrec][2] FP64 (time-major layout above)
+ * n may exceed max_solves (processed in chunks).  A source whose 6x6 stencil
+ * patch (Sec. 3.3.2 item 2) leaves the interior nodes 1 <= i <= nx-2,
+ * 0 <= j <= nz-2 yields NaN seismograms. */
+int oed_forward(oed_ctx *ctx, const double *theta, int n, double *g, void *stream);
+
+/* Gauss-Newton Hessians H_1 at n nodes (Thm 2 Eq. H1; Eq. H1_numerics) with
+ * C_eps = sigma^2 I and a central-FD Jacobian:
+ *   J_{m,r,c; j} = (g(theta + d_j e_j) - g(theta - d_j e_j)) / (2 d_j),
+ *   d_j = rel_step * (hi_j - lo_j).
+ * The 2*7 perturbed solves of every node run batched; the FP64 Jacobian
+ * subtraction and the FP64 J^T J accumulation are fused.
+ *   theta       device [n][7]
+ *   lo, hi      host [7] prior box (sets the FD steps)
+ *   win_levels  host [nwin] or NULL: window w covers levels m < win_levels[w]
+ *               (1 <= win_levels[w] <= nsteps+1, increasing)
+ *   H           device [n][7][7] FP64 over all levels (full symmetric matrix)
+ *   H_rec       device [n][nrec][nwin][28] or NULL: per receiver and window,
+ *               upper triangle row-major (requires win_levels)
+ *   status      device [n] or NULL: 0, or OED_EINVAL if a perturbed source
+ *               leaves the interior (its H is then NaN). */
+int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, const double *hi,
+                double rel_step, double sigma, const int *win_levels, int nwin, double *H,
+                double *H_rec, int *status, void *stream);
+
+/* Per-node gain and quadrature sum (Sec. 3.3.3, Thm 4, Eqs. intpoly / mcs):
+ *   S = sqrt(diag H_1), Ht = S^-1 H_1 S^-1 = L L^T (Cholesky, FP64),
+ *   log det H_1 = sum log H_ii + 2 sum log L_ii,
+ *   D_i = 1/2 log det H_1 - 7/2 (1 + log 2 pi) + sum_j log(hi_j - lo_j),
+ *   eig = sum over positive-definite nodes of w_i D_i (deterministic order).
+ *   H       device [n][7][7]
+ *   w       device [n] quadrature weights (may be negative for sparse grids)
+ *   lo, hi  host [7]
+ *   eig     device [1]
+ *   dkl     device [n] or NULL (0 for rejected nodes)
+ *   status  device [n] or NULL: 0 or OED_ENOTPD
+ *   n_bad   device [1] or NULL: number of rejected nodes
+ * ctx may be NULL (no workspace is used). */
+int oed_eig(oed_ctx *ctx, const double *H, int n, const double *w, const double *lo,
+            const double *hi, double *eig, double *dkl, int *status, int *n_bad, void *stream);
+
+/* EIG of many receiver designs from per-receiver partial Hessians (H_1 is
+ * additive over receivers and levels, Appendix C):
+ *   H_d(theta_i) = sum_{r : mask[d][r] != 0} H_rec[i][r][win]
+ *   H_rec   device [n][nrec][nwin][28] from oed_hessian
+ *   mask    device [ndesign][nrec] bytes
+ *   eig     device [ndesign]
+ *   n_bad   device [ndesign] or NULL */
+int oed_eig_designs(oed_ctx *ctx, const double *H_rec, int n, int nrec, int nwin, int win,
+                    const unsigned char *mask, int ndesign, const double *w, const double *lo,
+                    const double *hi, double *eig, int *n_bad, void *stream);
+
+/* Monte Carlo nodes (Eq. mcs): theta_i = lo + (hi - lo) u_i, w_i = 1/M.
+ *   u      device [M][7] uniform variates in [0, 1)
+ *   theta  device [M][7], w device [M] */
+int oed_nodes_mc(const double *u, int M, const double *lo, const double *hi, double *theta,
+                 double *w, void *stream);
+
+/* Smolyak sparse grid on [lo, hi] (Eq. intpoly): 1-D Gauss-Legendre rules of
+ * l + 1 points (l >= 0), total-degree index set level - dim + 1 <= |l| <= level,
+ * combination coefficients (-1)^(level-|l|) C(dim-1, level-|l|), coinciding
+ * nodes merged, weights for the uniform probability measure (sum 1).  Host call.
+ *   theta host [max_nodes][dim], w host [max_nodes] (may be NULL to count only)
+ *   count receives the number of nodes; OED_ENOMEM if it exceeds max_nodes. */
+int oed_nodes_smolyak(int dim, int level, const double *lo, const double *hi, int max_nodes,
+                      double *theta, double *w, int *count);
+
+/* Whole path with HOST buffers: copies theta and w to the device, runs
+ * oed_hessian and oed_eig on the context's own stream, copies the results back
+ * and synchronises.  theta host [n][7], w host [n], eig host [1], dkl host [n]
+ * or NULL, n_bad host [1] or NULL.  The device staging buffers live in the
+ * context and grow on demand. */
+int oed_eig_host(oed_ctx *ctx, const double *theta, const double *w, int n, const double *lo,
+                 const double *hi, double rel_step, double sigma, double *eig, double *dkl,
+                 int *n_bad);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OED_H */

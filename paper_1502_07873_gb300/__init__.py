@@ -1,0 +1,281 @@
+"""Python binding of liboed (include/oed.h): the GB300 (sm_103a) CUDA path of the
+Laplace-approximated expected information gain for seismic source inversion
+(Long, Motamed & Tempone, arXiv:1502.07873).
+
+This module only marshals arguments: every step of the computation runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  The
+functions carry the C names (``oed_forward``, ``oed_hessian``, ``oed_eig``,
+``oed_eig_designs``, ``oed_nodes_mc``, ``oed_nodes_smolyak``, ``oed_eig_host``);
+``Context`` owns an ``oed_ctx``.  If the shared library has not been built the
+import of any entry point raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboed.so")
+
+OED_OK, OED_EINVAL, OED_ENOMEM, OED_ENOTPD, OED_ECUDA, OED_ETIMEOUT = range(6)
+OED_FP32, OED_FP64 = 0, 1
+NTHETA = 7
+
+SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
+           "oed_status_string", "oed_chunk_nodes", "oed_forward", "oed_hessian", "oed_eig",
+           "oed_eig_designs", "oed_nodes_mc", "oed_nodes_smolyak", "oed_eig_host",
+           "oed_last_step_time")
+
+
+class OedError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_status_name(code)}: {msg}")
+        self.code = code
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nsteps", ctypes.c_int), ("nlayers", ctypes.c_int),
+                ("z_top", ctypes.POINTER(ctypes.c_double)), ("vp", ctypes.POINTER(ctypes.c_double)),
+                ("vs", ctypes.POINTER(ctypes.c_double)), ("rho", ctypes.POINTER(ctypes.c_double)),
+                ("nrec", ctypes.c_int), ("rec_ix", ctypes.POINTER(ctypes.c_int)),
+                ("precision", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library():
+    """Load liboed.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "oed_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(Problem), i]),
+        "oed_workspace_bytes": (sz, [ctypes.POINTER(Problem), i]),
+        "oed_destroy": (i, [vp]),
+        "oed_last_error": (ctypes.c_char_p, [vp]),
+        "oed_status_string": (ctypes.c_char_p, [i]),
+        "oed_chunk_nodes": (i, [vp]),
+        "oed_forward": (i, [vp, vp, i, vp, vp]),
+        "oed_hessian": (i, [vp, vp, i, dp, dp, d, d, ip, i, vp, vp, vp, vp]),
+        "oed_eig": (i, [vp, vp, i, vp, dp, dp, vp, vp, vp, vp, vp]),
+        "oed_eig_designs": (i, [vp, vp, i, i, i, i, vp, i, vp, dp, dp, vp, vp, vp]),
+        "oed_nodes_mc": (i, [vp, i, dp, dp, vp, vp, vp]),
+        "oed_nodes_smolyak": (i, [i, i, dp, dp, i, dp, dp, ip]),
+        "oed_eig_host": (i, [vp, dp, dp, i, dp, dp, d, d, dp, dp, ip]),
+        "oed_last_step_time": (i, [vp, ctypes.POINTER(ctypes.c_float), ip]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _status_name(code: int) -> str:
+    names = {0: "OED_OK", 1: "OED_EINVAL", 2: "OED_ENOMEM", 3: "OED_ENOTPD", 4: "OED_ECUDA",
+             5: "OED_ETIMEOUT"}
+    return names.get(code, f"status {code}")
+
+
+def _darr(vals):
+    a = (ctypes.c_double * len(vals))(*[float(v) for v in vals])
+    return a
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check(ctx_handle, rc: int, what: str):
+    if rc != OED_OK:
+        msg = library().oed_last_error(ctx_handle) if ctx_handle else b""
+        raise OedError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+
+def make_problem(nx, nz, h, dt, nsteps, layers, rec_ix, precision=OED_FP32):
+    """Build an oed_problem (keeps the host arrays alive on the returned object)."""
+    p = Problem()
+    p.nx, p.nz, p.h, p.dt, p.nsteps = int(nx), int(nz), float(h), float(dt), int(nsteps)
+    p.nlayers = len(layers)
+    p._z = _darr([l[0] for l in layers])
+    p._vp = _darr([l[1] for l in layers])
+    p._vs = _darr([l[2] for l in layers])
+    p._rho = _darr([l[3] for l in layers])
+    p.z_top, p.vp, p.vs, p.rho = p._z, p._vp, p._vs, p._rho
+    p.nrec = len(rec_ix)
+    p._rec = (ctypes.c_int * len(rec_ix))(*[int(r) for r in rec_ix])
+    p.rec_ix = p._rec
+    p.precision = int(precision)
+    return p
+
+
+def problem_from_workload(w, precision=OED_FP32, rec_ix=None, nsteps=None):
+    return make_problem(w.nx, w.nz, w.h, w.dt, w.nsteps if nsteps is None else nsteps, w.layers,
+                        w.rec_ix if rec_ix is None else rec_ix, precision)
+
+
+def oed_workspace_bytes(problem: Problem, max_solves: int) -> int:
+    return int(library().oed_workspace_bytes(ctypes.byref(problem), int(max_solves)))
+
+
+class Context:
+    """An oed_ctx: device workspace for up to ``max_solves`` concurrent solves."""
+
+    def __init__(self, problem: Problem, max_solves: int):
+        L = library()
+        self.problem = problem
+        self.handle = ctypes.c_void_p()
+        rc = L.oed_create(ctypes.byref(self.handle), ctypes.byref(problem), int(max_solves))
+        if rc != OED_OK:
+            raise OedError(rc, "oed_create failed")
+        self.max_solves = int(max_solves)
+        self.nrec = problem.nrec
+        self.nlev = problem.nsteps + 1
+
+    def close(self):
+        if self.handle:
+            library().oed_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def last_step_time(self):
+        """(milliseconds, launches) of the stencil launches of the last time loop."""
+        ms = ctypes.c_float()
+        n = ctypes.c_int()
+        _check(self.handle, library().oed_last_step_time(self.handle, ctypes.byref(ms), ctypes.byref(n)),
+               "oed_last_step_time")
+        return float(ms.value), int(n.value)
+
+    @property
+    def chunk_nodes(self) -> int:
+        return int(library().oed_chunk_nodes(self.handle))
+
+
+def oed_forward(ctx: Context, theta, g, stream=None):
+    """Seismograms g[n][nsteps+1][nrec][2] (FP64, device) of theta[n][7] (FP64, device)."""
+    n = theta.shape[0]
+    _check(ctx.handle, library().oed_forward(ctx.handle, _ptr(theta), n, _ptr(g), _stream(stream)),
+           "oed_forward")
+    return g
+
+
+def oed_hessian(ctx: Context, theta, lo: Sequence[float], hi: Sequence[float], rel_step: float,
+                sigma: float, H, win_levels: Optional[Sequence[int]] = None, H_rec=None,
+                status=None, stream=None):
+    """Gauss-Newton Hessians H[n][7][7] (device) from central-FD solves."""
+    n = theta.shape[0]
+    nwin = 0 if win_levels is None else len(win_levels)
+    wl = (ctypes.c_int * max(1, nwin))(*(win_levels or [0]))
+    rc = library().oed_hessian(ctx.handle, _ptr(theta), n, _darr(lo), _darr(hi), float(rel_step),
+                               float(sigma), wl if nwin else None, nwin, _ptr(H), _ptr(H_rec),
+                               _ptr(status), _stream(stream))
+    _check(ctx.handle, rc, "oed_hessian")
+    return H
+
+
+def oed_eig(ctx: Optional[Context], H, w, lo, hi, eig, dkl=None, status=None, n_bad=None,
+            stream=None):
+    """EIG = sum_i w_i D_KL-hat(H_i) into eig[1] (device)."""
+    n = H.shape[0]
+    h = ctx.handle if ctx is not None else None
+    rc = library().oed_eig(h, _ptr(H), n, _ptr(w), _darr(lo), _darr(hi), _ptr(eig), _ptr(dkl),
+                           _ptr(status), _ptr(n_bad), _stream(stream))
+    _check(h, rc, "oed_eig")
+    return eig
+
+
+def oed_eig_designs(ctx: Optional[Context], H_rec, win: int, mask, w, lo, hi, eig, n_bad=None,
+                    stream=None):
+    """EIG of every receiver design in mask[ndesign][nrec] from H_rec[n][nrec][nwin][28]."""
+    n, nrec, nwin = H_rec.shape[0], H_rec.shape[1], H_rec.shape[2]
+    h = ctx.handle if ctx is not None else None
+    rc = library().oed_eig_designs(h, _ptr(H_rec), n, nrec, nwin, int(win), _ptr(mask),
+                                   mask.shape[0], _ptr(w), _darr(lo), _darr(hi), _ptr(eig),
+                                   _ptr(n_bad), _stream(stream))
+    _check(h, rc, "oed_eig_designs")
+    return eig
+
+
+def oed_nodes_mc(u, lo, hi, theta, w, stream=None):
+    rc = library().oed_nodes_mc(_ptr(u), u.shape[0], _darr(lo), _darr(hi), _ptr(theta), _ptr(w),
+                                _stream(stream))
+    _check(None, rc, "oed_nodes_mc")
+    return theta, w
+
+
+def oed_nodes_smolyak(dim: int, level: int, lo=None, hi=None):
+    """Host call: (nodes [count][dim], weights [count]) as numpy arrays."""
+    import numpy as np
+    L = library()
+    cnt = ctypes.c_int()
+    lo_a = _darr(lo) if lo is not None else None
+    hi_a = _darr(hi) if hi is not None else None
+    rc = L.oed_nodes_smolyak(dim, level, lo_a, hi_a, 0, None, None, ctypes.byref(cnt))
+    _check(None, rc, "oed_nodes_smolyak")
+    x = np.zeros((cnt.value, dim))
+    w = np.zeros(cnt.value)
+    rc = L.oed_nodes_smolyak(dim, level, lo_a, hi_a, cnt.value,
+                             x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cnt))
+    _check(None, rc, "oed_nodes_smolyak")
+    return x, w
+
+
+def oed_eig_host(ctx: Context, theta, w, lo, hi, rel_step: float, sigma: float, want_dkl=False):
+    """Whole path with host arrays (numpy or pinned CPU tensors): returns (eig, dkl, n_bad)."""
+    import numpy as np
+
+    def hp(a):
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError("expected a contiguous CPU tensor")
+            return ctypes.cast(a.data_ptr(), ctypes.POINTER(ctypes.c_double))
+        return np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    th_keep = theta if hasattr(theta, "data_ptr") else np.ascontiguousarray(theta, dtype=np.float64)
+    w_keep = w if hasattr(w, "data_ptr") else np.ascontiguousarray(w, dtype=np.float64)
+    n = th_keep.shape[0]
+    eig = ctypes.c_double()
+    bad = ctypes.c_int()
+    dkl = np.zeros(n) if want_dkl else None
+    rc = library().oed_eig_host(ctx.handle, hp(th_keep), hp(w_keep), n, _darr(lo), _darr(hi),
+                                float(rel_step), float(sigma), ctypes.byref(eig),
+                                dkl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_dkl else None,
+                                ctypes.byref(bad))
+    _check(ctx.handle, rc, "oed_eig_host")
+    return eig.value, dkl, bad.value

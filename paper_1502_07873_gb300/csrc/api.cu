@@ -1,0 +1,406 @@
+// C ABI of liboed (include/oed.h): context, workspace, validation, chunking and
+// the captured CUDA graph that replays the time loop of a batch of solves.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "oed_internal.cuh"
+
+namespace oed {
+
+int set_err(oed_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_err(oed_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return OED_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return set_err(ctx, OED_ENOMEM, m);
+    return set_err(ctx, OED_ECUDA, m);
+}
+
+void hessian_init(cudaStream_t);
+int hsub_threads(int nrec);
+
+static bool problem_ok(const oed_problem *p, std::string *why)
+{
+    auto fail = [&](const char *m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (!p) return fail("problem is NULL");
+    if (p->nx < 8 || p->nz < 8) return fail("nx and nz must be >= 8");
+    if ((long long)p->nx * p->nz > (1LL << 30)) return fail("grid too large");
+    if (!(p->h > 0) || !(p->dt > 0) || !std::isfinite(p->h) || !std::isfinite(p->dt))
+        return fail("h and dt must be positive");
+    if (p->nsteps < 1 || p->nsteps > 1000000) return fail("nsteps must be in 1..1e6");
+    if (p->nlayers < 1 || p->nlayers > 64 || !p->z_top || !p->vp || !p->vs || !p->rho)
+        return fail("need 1..64 layers with z_top, vp, vs, rho");
+    if (p->z_top[0] != 0.0) return fail("z_top[0] must be 0");
+    for (int l = 0; l < p->nlayers; l++) {
+        if (l > 0 && !(p->z_top[l] > p->z_top[l - 1])) return fail("z_top must increase");
+        if (!(p->vp[l] > 0) || !(p->vs[l] > 0) || !(p->rho[l] > 0))
+            return fail("vp, vs, rho must be positive");
+        if (!(p->vp[l] * p->vp[l] >= 2.0 * p->vs[l] * p->vs[l]))
+            return fail("vp^2 >= 2 vs^2 required (lambda >= 0)");
+    }
+    if (p->nrec < 1 || p->nrec > kMaxRec || !p->rec_ix) return fail("nrec must be in 1..256");
+    for (int r = 0; r < p->nrec; r++)
+        if (p->rec_ix[r] < 0 || p->rec_ix[r] >= p->nx) return fail("receiver index outside 0..nx-1");
+    if (p->precision != OED_FP32 && p->precision != OED_FP64) return fail("precision must be OED_FP32 or OED_FP64");
+    return true;
+}
+
+static Geometry make_geometry(const oed_problem *p)
+{
+    Geometry g;
+    g.nx = p->nx;
+    g.nz = p->nz;
+    g.xp = (p->nx + 31) / 32 * 32;
+    g.nsteps = p->nsteps;
+    g.nlev = p->nsteps + 1;
+    g.nrec = p->nrec;
+    g.h = p->h;
+    g.dt = p->dt;
+    g.comp_stride = (size_t)g.nz * g.xp;
+    g.solve_stride = 2 * g.comp_stride;
+    return g;
+}
+
+struct Sizes {
+    size_t u, src, stf, trace, theta, rows, rec, hseg, total;
+};
+
+static Sizes sizes(const Geometry &g, int precision, int max_solves)
+{
+    const size_t e = precision == OED_FP64 ? 8 : 4;
+    const int chunk = std::max(1, max_solves / kNP);
+    Sizes s;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    s.u = al((size_t)max_solves * g.solve_stride * e);
+    s.src = al((size_t)max_solves * (precision == OED_FP64 ? sizeof(SourceDesc<double>)
+                                                           : sizeof(SourceDesc<float>)));
+    s.stf = al((size_t)max_solves * g.nsteps * e);
+    s.trace = al((size_t)max_solves * g.nlev * g.nrec * 2 * e);
+    s.theta = al((size_t)max_solves * kNT * sizeof(double));
+    s.rows = al((size_t)g.nz * (precision == OED_FP64 ? sizeof(RowCoef<double>) : sizeof(RowCoef<float>)));
+    s.rec = al((size_t)g.nrec * sizeof(int));
+    s.hseg = al((size_t)chunk * 16 * g.nrec * 28 * sizeof(double));
+    s.total = 2 * s.u + s.src + s.stf + s.trace + s.theta + s.rows + s.rec + s.hseg;
+    return s;
+}
+
+static void drop_graphs(oed_ctx *ctx)
+{
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+}
+
+// Run the time loop for nsolve solves on stream st, replaying a captured graph
+// (built on first use for this batch size).
+static int run_steps(oed_ctx *ctx, int nsolve, cudaStream_t st)
+{
+    auto it = ctx->graphs.find(nsolve);
+    if (it == ctx->graphs.end()) {
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamCreate");
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_err(ctx, e, "cudaStreamBeginCapture");
+        }
+        launch_forward_steps(ctx, nsolve, cap, ctx->ev_steps[0], ctx->ev_steps[1]);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cap, &graph);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamEndCapture");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "cudaGraphInstantiate");
+        it = ctx->graphs.emplace(nsolve, ex).first;
+    }
+    ctx->last_steps_launches = ctx->g.nsteps;
+    return cuda_err(ctx, cudaGraphLaunch(it->second, st), "cudaGraphLaunch");
+}
+
+}  // namespace oed
+
+using namespace oed;
+
+extern "C" {
+
+const char *oed_status_string(int status)
+{
+    switch (status) {
+    case OED_OK: return "OED_OK";
+    case OED_EINVAL: return "OED_EINVAL";
+    case OED_ENOMEM: return "OED_ENOMEM";
+    case OED_ENOTPD: return "OED_ENOTPD";
+    case OED_ECUDA: return "OED_ECUDA";
+    case OED_ETIMEOUT: return "OED_ETIMEOUT";
+    default: return "unknown";
+    }
+}
+
+size_t oed_workspace_bytes(const oed_problem *p, int max_solves)
+{
+    if (!problem_ok(p, nullptr) || max_solves < 1) return 0;
+    return sizes(make_geometry(p), p->precision, max_solves).total;
+}
+
+int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
+{
+    if (!out) return OED_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (!problem_ok(p, &why)) {
+        fprintf(stderr, "oed_create: %s\n", why.c_str());
+        return OED_EINVAL;
+    }
+    if (max_solves < kNP || max_solves > 65535) {
+        fprintf(stderr, "oed_create: max_solves must be in 15..65535\n");
+        return OED_EINVAL;
+    }
+    oed_ctx *ctx = new (std::nothrow) oed_ctx();
+    if (!ctx) return OED_ENOMEM;
+    ctx->g = make_geometry(p);
+    ctx->precision = p->precision;
+    ctx->elem = p->precision == OED_FP64 ? 8 : 4;
+    ctx->max_solves = max_solves;
+    cudaGetDevice(&ctx->device);
+    ctx->z_top.assign(p->z_top, p->z_top + p->nlayers);
+    ctx->vp.assign(p->vp, p->vp + p->nlayers);
+    ctx->vs.assign(p->vs, p->vs + p->nlayers);
+    ctx->rho.assign(p->rho, p->rho + p->nlayers);
+    ctx->rec_ix.assign(p->rec_ix, p->rec_ix + p->nrec);
+
+    const Sizes s = sizes(ctx->g, ctx->precision, max_solves);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete ctx;
+        return OED_ECUDA;
+    }
+    if (s.total > free_b) {
+        fprintf(stderr, "oed_create: workspace %zu B exceeds free device memory %zu B\n", s.total, free_b);
+        delete ctx;
+        return OED_ENOMEM;
+    }
+    char *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, s.total);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? OED_ENOMEM : OED_ECUDA;
+    }
+    ctx->bytes = s.total;
+    char *q = base;
+    ctx->d_u0 = q; q += s.u;
+    ctx->d_u1 = q; q += s.u;
+    ctx->d_src = q; q += s.src;
+    ctx->d_stf = q; q += s.stf;
+    ctx->d_trace = q; q += s.trace;
+    ctx->d_theta = (double *)q; q += s.theta;
+    ctx->d_rows = q; q += s.rows;
+    ctx->d_rec = (int *)q; q += s.rec;
+    ctx->d_hseg = (double *)q; q += s.hseg;
+    cudaMemcpy(ctx->d_rec, ctx->rec_ix.data(), sizeof(int) * p->nrec, cudaMemcpyHostToDevice);
+    cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+    cudaEventCreate(&ctx->ev_steps[0]);
+    cudaEventCreate(&ctx->ev_steps[1]);
+    hessian_init(ctx->own_stream);
+    launch_rows(ctx, ctx->own_stream);
+    e = cudaStreamSynchronize(ctx->own_stream);
+    if (e != cudaSuccess) {
+        int rc = cuda_err(ctx, e, "oed_create");
+        oed_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return OED_OK;
+}
+
+int oed_destroy(oed_ctx *ctx)
+{
+    if (!ctx) return OED_OK;
+    drop_graphs(ctx);
+    if (ctx->d_u0) cudaFree(ctx->d_u0);   // base of the single workspace allocation
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    for (int k = 0; k < 2; k++)
+        if (ctx->ev_steps[k]) cudaEventDestroy(ctx->ev_steps[k]);
+    cudaFree(ctx->h_stage_theta);
+    cudaFree(ctx->h_stage_w);
+    cudaFree(ctx->h_stage_H);
+    cudaFree(ctx->h_stage_dkl);
+    cudaFree(ctx->h_stage_eig);
+    cudaFree(ctx->h_stage_bad);
+    delete ctx;
+    return OED_OK;
+}
+
+const char *oed_last_error(const oed_ctx *ctx)
+{
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+int oed_last_step_time(const oed_ctx *ctx, float *ms, int *launches)
+{
+    if (!ctx || !ms) return OED_EINVAL;
+    *ms = 0.0f;
+    if (launches) *launches = ctx->last_steps_launches;
+    if (!ctx->last_steps_launches) return OED_OK;
+    cudaError_t e = cudaEventElapsedTime(ms, ctx->ev_steps[0], ctx->ev_steps[1]);
+    return e == cudaSuccess ? OED_OK : OED_ECUDA;
+}
+
+int oed_chunk_nodes(const oed_ctx *ctx)
+{
+    return ctx ? std::max(1, ctx->max_solves / kNP) : 0;
+}
+
+int oed_forward(oed_ctx *ctx, const double *theta, int n, double *g, void *stream)
+{
+    if (!ctx) return OED_EINVAL;
+    if (n < 0 || (n > 0 && (!theta || !g))) return set_err(ctx, OED_EINVAL, "oed_forward: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t per = (size_t)ctx->g.nlev * ctx->g.nrec * 2;
+    for (int off = 0; off < n; off += ctx->max_solves) {
+        const int nb = std::min(ctx->max_solves, n - off);
+        launch_sources(ctx, theta + (size_t)off * kNT, nb, 1, nullptr, st);
+        int rc = run_steps(ctx, nb, st);
+        if (rc) return rc;
+        launch_trace_to_f64(ctx, nb, g + (size_t)off * per, st);
+    }
+    return cuda_err(ctx, cudaGetLastError(), "oed_forward");
+}
+
+int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, const double *hi,
+                double rel_step, double sigma, const int *win_levels, int nwin, double *H,
+                double *H_rec, int *status, void *stream)
+{
+    if (!ctx) return OED_EINVAL;
+    if (n < 0 || (n > 0 && (!theta || !H)) || !lo || !hi)
+        return set_err(ctx, OED_EINVAL, "oed_hessian: bad pointer arguments");
+    if (!(rel_step > 0) || !(sigma > 0) || !std::isfinite(rel_step) || !std::isfinite(sigma))
+        return set_err(ctx, OED_EINVAL, "oed_hessian: rel_step and sigma must be positive");
+    if (nwin < 0 || nwin > 15 || (nwin > 0 && !win_levels) || (H_rec && nwin == 0))
+        return set_err(ctx, OED_EINVAL, "oed_hessian: 0..15 windows; H_rec needs windows");
+    double inv2d[kNT], d[kNT];
+    for (int j = 0; j < kNT; j++) {
+        if (!(hi[j] > lo[j])) return set_err(ctx, OED_EINVAL, "oed_hessian: need hi > lo");
+        d[j] = rel_step * (hi[j] - lo[j]);
+        inv2d[j] = 1.0 / (2.0 * d[j]);
+    }
+    // segment ends: the window ends (increasing), then all levels
+    std::vector<int> seg_end;
+    std::vector<int> win_seg(nwin);
+    for (int w = 0; w < nwin; w++) {
+        const int L = win_levels[w];
+        if (L < 1 || L > ctx->g.nlev || (w > 0 && L <= win_levels[w - 1]))
+            return set_err(ctx, OED_EINVAL, "oed_hessian: window levels must increase within 1..nsteps+1");
+        seg_end.push_back(L);
+        win_seg[w] = (int)seg_end.size() - 1;
+    }
+    if (seg_end.empty() || seg_end.back() != ctx->g.nlev) seg_end.push_back(ctx->g.nlev);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int chunk = oed_chunk_nodes(ctx);
+    for (int off = 0; off < n; off += chunk) {
+        const int nb = std::min(chunk, n - off);
+        launch_sources(ctx, theta + (size_t)off * kNT, nb, kNP, d, st);
+        int rc = run_steps(ctx, nb * kNP, st);
+        if (rc) return rc;
+        launch_hessian(ctx, nb, inv2d, sigma, seg_end.data(), (int)seg_end.size(), win_seg.data(),
+                       nwin, H + (size_t)off * 49,
+                       H_rec ? H_rec + (size_t)off * ctx->g.nrec * nwin * 28 : nullptr,
+                       status ? status + off : nullptr, st);
+    }
+    return cuda_err(ctx, cudaGetLastError(), "oed_hessian");
+}
+
+static double log_volume(const double *lo, const double *hi)
+{
+    double v = 0.0;
+    for (int j = 0; j < kNT; j++) v += std::log(hi[j] - lo[j]);
+    return v;
+}
+
+int oed_eig(oed_ctx *ctx, const double *H, int n, const double *w, const double *lo,
+            const double *hi, double *eig, double *dkl, int *status, int *n_bad, void *stream)
+{
+    if (n < 0 || (n > 0 && (!H || !w)) || !eig || !lo || !hi)
+        return set_err(ctx, OED_EINVAL, "oed_eig: bad arguments");
+    for (int j = 0; j < kNT; j++)
+        if (!(hi[j] > lo[j])) return set_err(ctx, OED_EINVAL, "oed_eig: need hi > lo");
+    launch_eig(H, n, w, log_volume(lo, hi), eig, dkl, status, n_bad, (cudaStream_t)stream);
+    return cuda_err(ctx, cudaGetLastError(), "oed_eig");
+}
+
+int oed_eig_designs(oed_ctx *ctx, const double *H_rec, int n, int nrec, int nwin, int win,
+                    const unsigned char *mask, int ndesign, const double *w, const double *lo,
+                    const double *hi, double *eig, int *n_bad, void *stream)
+{
+    if (n < 0 || nrec < 1 || nrec > kMaxRec || nwin < 1 || win < 0 || win >= nwin || ndesign < 0 ||
+        (n > 0 && (!H_rec || !w)) || (ndesign > 0 && (!mask || !eig)) || !lo || !hi)
+        return set_err(ctx, OED_EINVAL, "oed_eig_designs: bad arguments");
+    for (int j = 0; j < kNT; j++)
+        if (!(hi[j] > lo[j])) return set_err(ctx, OED_EINVAL, "oed_eig_designs: need hi > lo");
+    launch_eig_designs(H_rec, n, nrec, nwin, win, mask, ndesign, w, log_volume(lo, hi), eig, n_bad,
+                       (cudaStream_t)stream);
+    return cuda_err(ctx, cudaGetLastError(), "oed_eig_designs");
+}
+
+int oed_nodes_mc(const double *u, int M, const double *lo, const double *hi, double *theta,
+                 double *w, void *stream)
+{
+    if (M < 0 || (M > 0 && (!u || !theta || !w)) || !lo || !hi) return OED_EINVAL;
+    launch_nodes_mc(u, M, lo, hi, theta, w, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? OED_OK : OED_ECUDA;
+}
+
+int oed_eig_host(oed_ctx *ctx, const double *theta, const double *w, int n, const double *lo,
+                 const double *hi, double rel_step, double sigma, double *eig, double *dkl,
+                 int *n_bad)
+{
+    if (!ctx) return OED_EINVAL;
+    if (n < 1 || !theta || !w || !eig || !lo || !hi)
+        return set_err(ctx, OED_EINVAL, "oed_eig_host: bad arguments");
+    cudaStream_t st = ctx->own_stream;
+    if (n > ctx->h_stage_cap) {
+        cudaFree(ctx->h_stage_theta);
+        cudaFree(ctx->h_stage_w);
+        cudaFree(ctx->h_stage_H);
+        cudaFree(ctx->h_stage_dkl);
+        cudaFree(ctx->h_stage_eig);
+        cudaFree(ctx->h_stage_bad);
+        ctx->h_stage_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->h_stage_theta, sizeof(double) * kNT * n);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_stage_w, sizeof(double) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_stage_H, sizeof(double) * 49 * n);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_stage_dkl, sizeof(double) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_stage_eig, sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_stage_bad, sizeof(int));
+        if (e != cudaSuccess) return cuda_err(ctx, e, "oed_eig_host staging");
+        ctx->h_stage_cap = n;
+    }
+    cudaMemcpyAsync(ctx->h_stage_theta, theta, sizeof(double) * kNT * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ctx->h_stage_w, w, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    int rc = oed_hessian(ctx, ctx->h_stage_theta, n, lo, hi, rel_step, sigma, nullptr, 0,
+                         ctx->h_stage_H, nullptr, nullptr, st);
+    if (rc) return rc;
+    rc = oed_eig(ctx, ctx->h_stage_H, n, ctx->h_stage_w, lo, hi, ctx->h_stage_eig,
+                 dkl ? ctx->h_stage_dkl : nullptr, nullptr, ctx->h_stage_bad, st);
+    if (rc) return rc;
+    cudaMemcpyAsync(eig, ctx->h_stage_eig, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (dkl) cudaMemcpyAsync(dkl, ctx->h_stage_dkl, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    if (n_bad) cudaMemcpyAsync(n_bad, ctx->h_stage_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    return cuda_err(ctx, cudaStreamSynchronize(st), "oed_eig_host");
+}
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// Central finite-difference Jacobian and Gauss-Newton Hessian
+// H_1 = sum_{m,r} J_{m,r}^T C_eps^-1 J_{m,r}, C_eps = sigma^2 I
+// (Thm 2 Eq. H1; Eq. H1_numerics; Appendix C: H_1 is a sum over receivers and
+// time levels of rank-one terms, so per-receiver and per-window partial sums add up).
+//
+// Seismograms of the 15 solves of a node sit in trace[s][m][r][c] (stencil
+// precision).  The Jacobian column j is formed in FP64 from the +/- pair,
+//   J_j = (g_{+j} - g_{-j}) / (2 d_j),
+// and the 28 unique products are accumulated in FP64.  One block handles one
+// node and one time sub-segment; its threads walk the flattened (m, r, c) rows so
+// that a warp reads consecutive (r, c) of the same level (coalesced), and each
+// thread keeps a single (r, c) so its 28 partial sums belong to one receiver.
+#include "oed_internal.cuh"
+
+namespace oed {
+
+struct HArgs {
+    double inv2d[kNT];      // 1 / (2 d_j)
+    int sub_m0[16];         // sub-segment level ranges [m0, m1)
+    int sub_m1[16];
+    int win_sub_end[16];    // window w ends with sub-segment win_sub_end[w] - 1
+    int nsub;
+};
+
+template <typename real>
+__global__ void __launch_bounds__(512) k_hsub(const real *__restrict__ trace, Geometry g,
+                                              HArgs a, double *__restrict__ hsub)
+{
+    const int node = blockIdx.x, sub = blockIdx.y;
+    const int nq = 2 * g.nrec;                // (r, c) pairs per level
+    const int lanes = blockDim.x / nq;        // threads per (r, c)
+    const int t = threadIdx.x;
+    const int q = t % nq, mo = t / nq;
+    double acc[28];
+#pragma unroll
+    for (int k = 0; k < 28; k++) acc[k] = 0.0;
+    const size_t per_solve = (size_t)g.nlev * nq;
+    const real *base = trace + (size_t)node * kNP * per_solve;
+    if (mo < lanes) {
+        for (int m = a.sub_m0[sub] + mo; m < a.sub_m1[sub]; m += lanes) {
+            const size_t off = (size_t)m * nq + q;
+            double J[kNT];
+#pragma unroll
+            for (int j = 0; j < kNT; j++) {
+                const double gp = (double)base[(size_t)(1 + 2 * j) * per_solve + off];
+                const double gm = (double)base[(size_t)(2 + 2 * j) * per_solve + off];
+                J[j] = (gp - gm) * a.inv2d[j];
+            }
+            int k = 0;
+#pragma unroll
+            for (int x = 0; x < kNT; x++)
+#pragma unroll
+                for (int y = x; y < kNT; y++) acc[k++] += J[x] * J[y];
+        }
+    }
+    // per (r, c): sum over the lanes, then the two components of each receiver
+    extern __shared__ double sh[];   // [blockDim.x][29] (padded)
+#pragma unroll
+    for (int k = 0; k < 28; k++) sh[t * 29 + k] = acc[k];
+    __syncthreads();
+    const int nrec = g.nrec;
+    for (int w = t; w < nrec * 28; w += blockDim.x) {
+        const int r = w / 28, k = w % 28;
+        double v = 0.0;
+        for (int l = 0; l < lanes; l++)
+            v += sh[(l * nq + 2 * r) * 29 + k] + sh[(l * nq + 2 * r + 1) * 29 + k];
+        hsub[(((size_t)node * a.nsub + sub) * nrec + r) * 28 + k] = v;
+    }
+}
+
+// Sum the sub-segments into per-receiver cumulative windows and the total H.
+template <typename real>
+__global__ void k_hcombine(const double *__restrict__ hsub, Geometry g, double s2, int nwin, HArgs a,
+                           const SourceDesc<real> *__restrict__ src, double *__restrict__ H,
+                           double *__restrict__ H_rec, int *__restrict__ status)
+{
+    const int node = blockIdx.x;
+    const int nrec = g.nrec;
+    const int nsub = a.nsub;
+    __shared__ double tot[28];
+    __shared__ int ok;
+    if (threadIdx.x < 28) tot[threadIdx.x] = 0.0;
+    if (threadIdx.x == 0) {
+        int o = 1;
+        for (int p = 0; p < kNP; p++) o &= src[(size_t)node * kNP + p].ok;
+        ok = o;
+    }
+    __syncthreads();
+    const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+    // per receiver, per window (cumulative over sub-segments), and the total
+    for (int w = threadIdx.x; w < nrec * 28; w += blockDim.x) {
+        const int r = w / 28, k = w % 28;
+        double run = 0.0;
+        int next = 0;
+        for (int sub = 0; sub < nsub; sub++) {
+            run += hsub[(((size_t)node * nsub + sub) * nrec + r) * 28 + k];
+            while (next < nwin && a.win_sub_end[next] == sub + 1) {
+                if (H_rec)
+                    H_rec[(((size_t)node * nrec + r) * nwin + next) * 28 + k] = ok ? s2 * run : nan;
+                next++;
+            }
+        }
+    }
+    // total over receivers and sub-segments in a fixed order (28 threads)
+    if (threadIdx.x < 28) {
+        const int k = threadIdx.x;
+        double v = 0.0;
+        for (int r = 0; r < nrec; r++)
+            for (int sub = 0; sub < nsub; sub++)
+                v += hsub[(((size_t)node * nsub + sub) * nrec + r) * 28 + k];
+        tot[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 49) {
+        const int x = threadIdx.x / 7, y = threadIdx.x % 7;
+        const int a0 = x < y ? x : y, b0 = x < y ? y : x;
+        const int k = a0 * 7 - a0 * (a0 - 1) / 2 + (b0 - a0);
+        H[(size_t)node * 49 + threadIdx.x] = ok ? s2 * tot[k] : nan;
+    }
+    if (threadIdx.x == 0 && status) status[node] = ok ? 0 : OED_EINVAL;
+}
+
+int hsub_threads(int nrec);
+
+void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double sigma,
+                    const int *seg_end, int nseg, const int *win_seg, int nwin, double *H,
+                    double *H_rec, int *status, cudaStream_t st)
+{
+    // Split the level range into at most 16 sub-segments that respect the window
+    // boundaries seg_end[0..nseg) (seg_end[nseg-1] = nlev), enough for >= ~4 blocks per SM.
+    const Geometry &g = ctx->g;
+    HArgs a;
+    for (int j = 0; j < kNT; j++) a.inv2d[j] = inv2d[j];
+    int want = 16;
+    int per = want / nseg;
+    if (per < 1) per = 1;
+    int nsub = 0;
+    int m0 = 0;
+    for (int sgi = 0; sgi < nseg; sgi++) {
+        const int m1 = seg_end[sgi];
+        const int len = m1 - m0;
+        int parts = per < len ? per : (len > 0 ? len : 1);
+        if (nsub + parts > 16 - (nseg - 1 - sgi)) parts = 16 - (nseg - 1 - sgi) - nsub;
+        if (parts < 1) parts = 1;
+        for (int p = 0; p < parts; p++) {
+            a.sub_m0[nsub] = m0 + (int)((long long)len * p / parts);
+            a.sub_m1[nsub] = m0 + (int)((long long)len * (p + 1) / parts);
+            nsub++;
+        }
+        for (int w = 0; w < nwin; w++)
+            if (win_seg[w] == sgi) a.win_sub_end[w] = nsub;
+        m0 = m1;
+    }
+    a.nsub = nsub;
+    const int threads = hsub_threads(g.nrec);
+    const size_t smem = (size_t)threads * 29 * sizeof(double);
+    dim3 grid(nnode, nsub);
+    if (ctx->precision == OED_FP64)
+        k_hsub<double><<<grid, threads, smem, st>>>((const double *)ctx->d_trace, g, a, ctx->d_hseg);
+    else
+        k_hsub<float><<<grid, threads, smem, st>>>((const float *)ctx->d_trace, g, a, ctx->d_hseg);
+    const double s2 = 1.0 / (sigma * sigma);
+    if (ctx->precision == OED_FP64)
+        k_hcombine<double><<<nnode, 256, 0, st>>>(ctx->d_hseg, g, s2, nwin, a,
+                                                  (const SourceDesc<double> *)ctx->d_src, H, H_rec,
+                                                  status);
+    else
+        k_hcombine<float><<<nnode, 256, 0, st>>>(ctx->d_hseg, g, s2, nwin, a,
+                                                 (const SourceDesc<float> *)ctx->d_src, H, H_rec,
+                                                 status);
+}
+
+int hsub_threads(int nrec)
+{
+    const int nq = 2 * nrec;
+    int lanes = 128 / nq;
+    if (lanes < 1) lanes = 1;
+    return lanes * nq;
+}
+
+void hessian_init(cudaStream_t)
+{
+    const int smem = 512 * 29 * (int)sizeof(double);
+    cudaFuncSetAttribute(k_hsub<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_hsub<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+}  // namespace oed

@@ -1,0 +1,200 @@
+// Scaled log-determinant, per-node information gain and quadrature sums (FP64).
+//
+//   S = sqrt(diag H_1), Ht = S^-1 H_1 S^-1 (Sec. 3.3.3: the scaling that takes the
+//   condition number from ~1e30 to O(10)), Ht = L L^T (Cholesky),
+//   log det H_1 = sum_i log H_ii + 2 sum_i log L_ii,
+//   D_KL-hat = 1/2 log det H_1 - N/2 log(2 pi) - N/2 - h(theta)   (Thm 4, Eq. DKL_hat)
+//   with the uniform-prior log-density h = -sum_j log(hi_j - lo_j),
+//   EIG = sum_i w_i D_i                                          (Eqs. intpoly / mcs).
+// Sums run in a fixed order, so a result does not depend on scheduling.
+#include "oed_internal.cuh"
+
+namespace oed {
+
+// Returns 0 and *logdet, or 1 if H is not positive definite (or not finite).
+// H is read through an accessor so both the full 7x7 and the packed 28 forms work.
+template <typename Get>
+__device__ int scaled_logdet7(Get Hij, double *logdet)
+{
+    double S[kNT], L[kNT][kNT];
+    double ld = 0.0;
+#pragma unroll
+    for (int i = 0; i < kNT; i++) {
+        const double d = Hij(i, i);
+        if (!(d > 0.0) || !isfinite(d)) return 1;
+        S[i] = sqrt(d);
+        ld += log(d);
+    }
+#pragma unroll
+    for (int j = 0; j < kNT; j++) {
+        double s = Hij(j, j) / (S[j] * S[j]);
+#pragma unroll
+        for (int k = 0; k < j; k++) s -= L[j][k] * L[j][k];
+        if (!(s > 0.0) || !isfinite(s)) return 1;
+        const double ljj = sqrt(s);
+        L[j][j] = ljj;
+        ld += 2.0 * log(ljj);
+#pragma unroll
+        for (int i = j + 1; i < kNT; i++) {
+            double t = Hij(i, j) / (S[i] * S[j]);
+#pragma unroll
+            for (int k = 0; k < j; k++) t -= L[i][k] * L[j][k];
+            L[i][j] = t / ljj;
+        }
+    }
+    *logdet = ld;
+    return 0;
+}
+
+__device__ __forceinline__ int upper_index(int a, int b)
+{
+    if (a > b) {
+        const int t = a;
+        a = b;
+        b = t;
+    }
+    return a * kNT - a * (a - 1) / 2 + (b - a);
+}
+
+// D_KL-hat from log det H_1 (N = 7): 1/2 logdet - 7/2 (log 2 pi + 1) + logvol
+__device__ __forceinline__ double dkl_from_logdet(double ld, double logvol)
+{
+    const double c = 3.5 * (1.8378770664093453 + 1.0);   // 7/2 (log(2 pi) + 1)
+    return 0.5 * ld - c + logvol;
+}
+
+// Whole quadrature in one block, deterministic: thread t takes the contiguous node
+// slice [t*per, (t+1)*per), computes each node's log-determinant and gain in order,
+// then the block adds the per-thread sums with a fixed tree.
+__global__ void __launch_bounds__(1024) k_eig(const double *__restrict__ H, int n,
+                                              const double *__restrict__ w, double logvol,
+                                              double *__restrict__ eig, double *__restrict__ dkl,
+                                              int *__restrict__ status, int *__restrict__ n_bad)
+{
+    __shared__ double sv[1024];
+    __shared__ int sb[1024];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int per = (n + T - 1) / T;
+    double v = 0.0;
+    int b = 0;
+    for (int i = t * per; i < (t + 1) * per && i < n; i++) {
+        const double *h = H + (size_t)i * 49;
+        double ld = 0.0;
+        const int bad = scaled_logdet7([&](int x, int y) { return h[x * 7 + y]; }, &ld);
+        const double D = bad ? 0.0 : dkl_from_logdet(ld, logvol);
+        if (!bad) v += w[i] * D;
+        b += bad;
+        if (dkl) dkl[i] = D;
+        if (status) status[i] = bad ? OED_ENOTPD : 0;
+    }
+    sv[t] = v;
+    sb[t] = b;
+    __syncthreads();
+    for (int s = T / 2; s > 0; s >>= 1) {
+        if (t < s) {
+            sv[t] += sv[t + s];
+            sb[t] += sb[t + s];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        *eig = sv[0];
+        if (n_bad) *n_bad = sb[0];
+    }
+}
+
+// One block per design: every thread takes nodes i = t, t + T, ..., builds
+// H = sum over the design's receivers of H_rec[i][r][win], and accumulates w_i D_i.
+__global__ void __launch_bounds__(256) k_designs(const double *__restrict__ H_rec, int n, int nrec,
+                                                 int nwin, int win,
+                                                 const unsigned char *__restrict__ mask,
+                                                 const double *__restrict__ w, double logvol,
+                                                 double *__restrict__ eig, int *__restrict__ n_bad)
+{
+    const int d = blockIdx.x;
+    extern __shared__ int sel[];   // receivers of this design, then reduction scratch
+    __shared__ int nsel;
+    __shared__ double sv[256];
+    __shared__ int sb[256];
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int r = 0; r < nrec; r++)
+            if (mask[(size_t)d * nrec + r]) sel[c++] = r;
+        nsel = c;
+    }
+    __syncthreads();
+    double v = 0.0;
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double h[28];
+#pragma unroll
+        for (int k = 0; k < 28; k++) h[k] = 0.0;
+        for (int q = 0; q < nsel; q++) {
+            const double *p = H_rec + (((size_t)i * nrec + sel[q]) * nwin + win) * 28;
+#pragma unroll
+            for (int k = 0; k < 28; k++) h[k] += p[k];
+        }
+        double ld = 0.0;
+        const int b = scaled_logdet7([&](int a, int c) { return h[upper_index(a, c)]; }, &ld);
+        if (b)
+            bad++;
+        else
+            v += w[i] * dkl_from_logdet(ld, logvol);
+    }
+    sv[threadIdx.x] = v;
+    sb[threadIdx.x] = bad;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sv[threadIdx.x] += sv[threadIdx.x + s];
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        eig[d] = sv[0];
+        if (n_bad) n_bad[d] = sb[0];
+    }
+}
+
+struct LoHi {
+    double v[2 * kNT];
+};
+
+__global__ void k_nodes_mc_v(const double *__restrict__ u, int M, LoHi lh, double *__restrict__ theta,
+                             double *__restrict__ w)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M * kNT) return;
+    const int j = k % kNT;
+    theta[k] = lh.v[j] + (lh.v[kNT + j] - lh.v[j]) * u[k];
+    if (j == 0) w[k / kNT] = 1.0 / M;
+}
+
+void launch_eig(const double *H, int n, const double *w, double logvol, double *eig, double *dkl,
+                int *status, int *n_bad, cudaStream_t s)
+{
+    k_eig<<<1, 1024, 0, s>>>(H, n, w, logvol, eig, dkl, status, n_bad);
+}
+
+void launch_eig_designs(const double *H_rec, int n, int nrec, int nwin, int win,
+                        const unsigned char *mask, int ndesign, const double *w, double logvol,
+                        double *eig, int *n_bad, cudaStream_t s)
+{
+    if (ndesign <= 0) return;
+    k_designs<<<ndesign, 256, sizeof(int) * nrec, s>>>(H_rec, n, nrec, nwin, win, mask, w, logvol,
+                                                      eig, n_bad);
+}
+
+void launch_nodes_mc(const double *u, int M, const double *lo, const double *hi, double *theta,
+                     double *w, cudaStream_t s)
+{
+    LoHi lh;
+    for (int j = 0; j < kNT; j++) {
+        lh.v[j] = lo[j];
+        lh.v[kNT + j] = hi[j];
+    }
+    if (M > 0) k_nodes_mc_v<<<(M * kNT + 255) / 256, 256, 0, s>>>(u, M, lh, theta, w);
+}
+
+}  // namespace oed

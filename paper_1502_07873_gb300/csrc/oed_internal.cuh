@@ -1,0 +1,131 @@
+// Internal declarations shared by the CUDA translation units of liboed.
+// Kernels and host launchers for the Laplace expected-information-gain path
+// (arXiv:1502.07873); the public C ABI is include/oed.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/oed.h"
+
+namespace oed {
+
+constexpr int kNT = 7;    // source parameters
+constexpr int kNP = 15;   // solves per node: centre and +/- d_j e_j
+constexpr int kMaxRec = 256;
+
+// Per-row stencil coefficients of the leap-frog update (Eq. Full_Disc) for a
+// medium that is constant along each grid row (layered in depth).  Every
+// coefficient is premultiplied by dt^2 / nu_j so the kernel adds
+// coefficient * (difference of neighbours) directly to 2u^m - u^{m-1}.
+//   interior rows 1..nz-2:
+//     Ax = axx (x_e - 2x_c + x_w) + axzp (x_s - x_c) - axzm (x_c - x_n)
+//        + lx ((z_se - z_ne) - (z_sw - z_nw)) + mxp (z_se - z_sw) - mxm (z_ne - z_nw)
+//     Az = azx (z_e - 2z_c + z_w) + azzp (z_s - z_c) - azzm (z_c - z_n)
+//        + mz ((x_se - x_ne) - (x_sw - x_nw)) + lzp (x_se - x_sw) - lzm (x_ne - x_nw)
+//   surface row 0 (summation-by-parts closure, "s" = row 1):
+//     Ax = axx (..) + axzp (x_s - x_c) + lx ((z_se - z_e) - (z_sw - z_w))
+//        + mxm (z_e - z_w) + mxp (z_se - z_sw)
+//     Az = azx (..) + azzp (z_s - z_c) + mz ((x_se - x_e) - (x_sw - x_w))
+//        + lzm (x_e - x_w) + lzp (x_se - x_sw)
+//   rf = dt^2/nu_j multiplies the force density; cp, cs = c dt / h for the
+//   absorbing rows (side columns of this row; the whole bottom row).
+template <typename real>
+struct RowCoef {
+    real axx, azx, axzp, axzm, azzp, azzm, lx, mxp, mxm, mz, lzp, lzm, rf, cp, cs, pad;
+};
+
+// Source of one solve: corner of the 6x6 patch and the spatial force density
+// f_x, f_z (Eq. source with the regularised delta / delta' of Sec. 3.3.2),
+// already multiplied by dt^2/nu of the patch rows.
+template <typename real>
+struct SourceDesc {
+    int i0, j0, ok, pad;
+    real wx[36];
+    real wz[36];
+};
+
+struct Geometry {
+    int nx, nz, xp;        // nodes, padded row stride (multiple of 32)
+    int nsteps, nlev;      // steps, levels = nsteps + 1
+    int nrec;
+    double h, dt;
+    size_t comp_stride;    // elements per component of one solve (nz * xp)
+    size_t solve_stride;   // 2 * comp_stride
+};
+
+struct StepTuning {
+    int zs;      // rows marched per thread
+    int wz;      // warps along z in a block
+};
+
+}  // namespace oed
+
+struct oed_ctx {
+    oed::Geometry g;
+    int precision;
+    int max_solves;
+    int device;
+    size_t elem;               // 4 or 8
+    std::vector<double> z_top, vp, vs, rho;
+    std::vector<int> rec_ix;
+    // device workspace
+    void *d_rows = nullptr;    // RowCoef<real>[nz]
+    int *d_rec = nullptr;      // [nrec]
+    void *d_u0 = nullptr;      // wavefield level buffer A [max_solves][2][nz][xp]
+    void *d_u1 = nullptr;      // wavefield level buffer B
+    void *d_src = nullptr;     // SourceDesc<real>[max_solves]
+    void *d_stf = nullptr;     // real [max_solves][nsteps]
+    void *d_trace = nullptr;   // real [max_solves][nlev][nrec][2]
+    double *d_theta = nullptr; // [max_solves][7] perturbed parameters
+    double *d_hseg = nullptr;  // [chunk][nrec][nseg_max][28] partial Hessians
+    int nseg_max = 0;
+    size_t bytes = 0;
+    oed::StepTuning tune{8, 4};
+    // host-path staging
+    cudaStream_t own_stream = nullptr;
+    double *h_stage_theta = nullptr, *h_stage_w = nullptr, *h_stage_H = nullptr,
+           *h_stage_dkl = nullptr, *h_stage_eig = nullptr;
+    int *h_stage_bad = nullptr;
+    int h_stage_cap = 0;
+    std::map<int, cudaGraphExec_t> graphs;   // nsolve -> captured time loop
+    cudaEvent_t ev_steps[2] = {nullptr, nullptr};   // recorded around the stencil launches
+    int last_steps_launches = 0;
+    std::string err;
+};
+
+namespace oed {
+
+int set_err(oed_ctx *ctx, int code, const std::string &msg);
+int cuda_err(oed_ctx *ctx, cudaError_t e, const char *what);
+
+// source.cu
+void launch_sources(const oed_ctx *ctx, const double *theta_nodes, int nnode, int per_node,
+                    const double *step, cudaStream_t s);
+void launch_rows(oed_ctx *ctx, cudaStream_t s);
+
+// stencil.cu
+void launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t s, cudaEvent_t ev0,
+                          cudaEvent_t ev1);
+void launch_trace_to_f64(const oed_ctx *ctx, int nsolve, double *g, cudaStream_t s);
+
+// hessian.cu
+void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double sigma,
+                    const int *seg_end, int nseg, const int *win_seg, int nwin, double *H,
+                    double *H_rec, int *status, cudaStream_t s);
+
+// logdet.cu
+void launch_eig(const double *H, int n, const double *w, double logvol, double *eig,
+                double *dkl, int *status, int *n_bad, cudaStream_t s);
+void launch_eig_designs(const double *H_rec, int n, int nrec, int nwin, int win,
+                        const unsigned char *mask, int ndesign, const double *w, double logvol,
+                        double *eig, int *n_bad, cudaStream_t s);
+void launch_nodes_mc(const double *u, int M, const double *lo, const double *hi, double *theta,
+                     double *w, cudaStream_t s);
+
+}  // namespace oed

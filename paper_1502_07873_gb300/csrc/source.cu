@@ -1,0 +1,223 @@
+// Source discretisation and medium coefficients (device side).
+//
+//  - k_sources: for every solve, the perturbed parameter vector theta +/- d_j e_j
+//    (central finite differences, 2*7 + 1 solves per node), the regularised
+//    delta / delta' weights of Sec. 3.3.2 item 2 (six points k-2..k+3, fourth-order
+//    moments, C^2 in x_s) combined into the force density f = M grad(delta)
+//    (Eq. source), and the Gaussian source time function of Sec. 4.1
+//    S(t) = w/sqrt(2 pi) exp(-w^2 (t - t_s)^2 / 2) sampled at every step.
+//    All of it in FP64, stored in the stencil's precision.
+//  - k_rows: per-row stencil coefficients of the leap-frog update for a medium
+//    layered in depth (lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2, Sec. 2.1).
+#include "oed_internal.cuh"
+
+namespace oed {
+
+// Regularised delta and delta' at nodes k-2..k+3 for offset a = (x_s - x_k)/h
+// (Sec. 3.3.2 item 2).  Horner form of the printed polynomials.
+__device__ void delta_weights(double a, double h, double *d, double *dp)
+{
+    const double P = a * a * a * a * a *
+                     (5.0 / 3.0 + a * (-7.0 / 24.0 + a * (-17.0 / 12.0 + a * (9.0 / 8.0 - a / 4.0))));
+    const double R = a * a * a * a * (-25.0 / 12.0 + a * (-3.0 / 4.0 + a * (59.0 / 12.0 + a * (-4.0 + a))));
+    const double ih = 1.0 / h, ih2 = ih * ih;
+    d[0] = (a * (1.0 / 12.0 + a * (-1.0 / 24.0 + a * (-1.0 / 12.0 - 19.0 / 24.0 * a))) + P) * ih;
+    d[1] = (a * (-2.0 / 3.0 + a * (2.0 / 3.0 + a * (1.0 / 6.0 + 4.0 * a))) - 5.0 * P) * ih;
+    d[2] = (1.0 + a * a * (-5.0 / 4.0 - 97.0 / 12.0 * a * a) + 10.0 * P) * ih;
+    d[3] = (a * (2.0 / 3.0 + a * (2.0 / 3.0 + a * (-1.0 / 6.0 + 49.0 / 6.0 * a))) - 10.0 * P) * ih;
+    d[4] = (a * (-1.0 / 12.0 + a * (-1.0 / 24.0 + a * (1.0 / 12.0 - 33.0 / 8.0 * a))) + 5.0 * P) * ih;
+    d[5] = (5.0 / 6.0 * a * a * a * a - P) * ih;
+    dp[0] = (-1.0 / 12.0 + a * (1.0 / 12.0 + a * (1.0 / 4.0 + 2.0 / 3.0 * a)) + R) * ih2;
+    dp[1] = (2.0 / 3.0 + a * (-4.0 / 3.0 + a * (-1.0 / 2.0 - 7.0 / 2.0 * a)) - 5.0 * R) * ih2;
+    dp[2] = (a * (5.0 / 2.0 + 22.0 / 3.0 * a * a) + 10.0 * R) * ih2;
+    dp[3] = (-2.0 / 3.0 + a * (-4.0 / 3.0 + a * (1.0 / 2.0 - 23.0 / 3.0 * a)) - 10.0 * R) * ih2;
+    dp[4] = (1.0 / 12.0 + a * (1.0 / 12.0 + a * (-1.0 / 4.0 + 4.0 * a)) + 5.0 * R) * ih2;
+    dp[5] = (-5.0 / 6.0 * a * a * a - R) * ih2;
+}
+
+struct FdStep {
+    double d[kNT];
+};
+
+// One thread block per solve.  Thread 0..35 fill the 6x6 patch; all threads
+// sample the source time function.
+template <typename real>
+__global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, int per_node,
+                          FdStep step, Geometry g, const RowCoef<real> *__restrict__ rows,
+                          SourceDesc<real> *__restrict__ src, real *__restrict__ stf,
+                          double *__restrict__ theta_out)
+{
+    const int s = blockIdx.x;
+    if (s >= nsolve) return;
+    const int node = s / per_node, p = s % per_node;
+    __shared__ double th[kNT];
+    __shared__ double wts[4][6];   // dx, dpx, dz, dpz
+    __shared__ int corner[3];
+    if (threadIdx.x < kNT) {
+        double v = theta_nodes[(size_t)node * kNT + threadIdx.x];
+        // p = 0 centre, p = 1 + 2j: +d_j, p = 2 + 2j: -d_j
+        if (p > 0) {
+            int j = (p - 1) >> 1;
+            if ((int)threadIdx.x == j) v += ((p - 1) & 1) ? -step.d[j] : step.d[j];
+        }
+        th[threadIdx.x] = v;
+        theta_out[(size_t)s * kNT + threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double qx = th[0] / g.h, qz = th[1] / g.h;
+        const double fx = floor(qx), fz = floor(qz);
+        int ok = isfinite(qx) && isfinite(qz) && fx > -1e9 && fx < 1e9 && fz > -1e9 && fz < 1e9;
+        int kx = ok ? (int)fx : 0, kz = ok ? (int)fz : 0;
+        double dx[6], dpx[6], dz[6], dpz[6];
+        delta_weights(qx - fx, g.h, dx, dpx);
+        delta_weights(qz - fz, g.h, dz, dpz);
+        for (int a = 0; a < 6; a++) {
+            wts[0][a] = dx[a];
+            wts[1][a] = dpx[a];
+            wts[2][a] = dz[a];
+            wts[3][a] = dpz[a];
+        }
+        const int i0 = kx - 2, j0 = kz - 2;
+        ok = ok && i0 >= 1 && i0 + 5 <= g.nx - 2 && j0 >= 0 && j0 + 5 <= g.nz - 2;
+        corner[0] = ok ? i0 : -100;
+        corner[1] = ok ? j0 : -100;
+        corner[2] = ok;
+        src[s].i0 = corner[0];
+        src[s].j0 = corner[1];
+        src[s].ok = ok;
+    }
+    __syncthreads();
+    if (threadIdx.x < 36) {
+        const int a = threadIdx.x % 6, b = threadIdx.x / 6;
+        const double mxx = th[4], mxz = th[5], mzz = th[6];
+        // f_x = m_xx delta'(x) delta(z) + m_xz delta(x) delta'(z)
+        // f_z = m_xz delta'(x) delta(z) + m_zz delta(x) delta'(z)
+        const double fx = mxx * wts[1][a] * wts[2][b] + mxz * wts[0][a] * wts[3][b];
+        const double fz = mxz * wts[1][a] * wts[2][b] + mzz * wts[0][a] * wts[3][b];
+        const int j = corner[1] + b;
+        const double rf = corner[2] ? (double)rows[j].rf : 0.0;
+        src[s].wx[threadIdx.x] = (real)(fx * rf);
+        src[s].wz[threadIdx.x] = (real)(fz * rf);
+    }
+    const double ts = th[2], ws = th[3];
+    const double c = ws * 0.3989422804014327;   // w / sqrt(2 pi)
+    const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+    for (int m = threadIdx.x; m < g.nsteps; m += blockDim.x) {
+        const double t = m * g.dt - ts;
+        double v = c * exp(-0.5 * ws * ws * t * t);
+        if (!corner[2]) v = nan;   // invalid source: poison the solve
+        stf[(size_t)s * g.nsteps + m] = (real)v;
+    }
+}
+
+// Per-row coefficients (one thread per row).
+template <typename real>
+__global__ void k_rows(Geometry g, int nlayers, const double *__restrict__ lay,
+                       RowCoef<real> *__restrict__ rows)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.nz) return;
+    auto layer_of = [&](int jj) {
+        const double z = (jj < 0 ? 0 : (jj >= g.nz ? g.nz - 1 : jj)) * g.h;
+        int l = 0;
+        for (int q = 0; q < nlayers; q++)
+            if (z >= lay[q]) l = q;
+        return l;
+    };
+    auto lam = [&](int jj) {
+        int l = layer_of(jj);
+        double vp = lay[nlayers + l], vs = lay[2 * nlayers + l], rho = lay[3 * nlayers + l];
+        return rho * (vp * vp - 2.0 * vs * vs);
+    };
+    auto mu = [&](int jj) {
+        int l = layer_of(jj);
+        double vs = lay[2 * nlayers + l], rho = lay[3 * nlayers + l];
+        return rho * vs * vs;
+    };
+    const int l = layer_of(j);
+    const double vp = lay[nlayers + l], vs = lay[2 * nlayers + l], rho = lay[3 * nlayers + l];
+    const double h2 = g.h * g.h;
+    const double r = g.dt * g.dt / rho;
+    const double lc = lam(j), mc = mu(j), pc = lc + 2.0 * mc;
+    RowCoef<double> c;
+    c.axx = pc * r / h2;
+    c.azx = mc * r / h2;
+    c.rf = r;
+    c.cp = vp * g.dt / g.h;
+    c.cs = vs * g.dt / g.h;
+    c.pad = 0.0;
+    if (j == 0) {
+        const double l1 = lam(1), m1 = mu(1), p1 = l1 + 2.0 * m1;
+        c.axzp = 2.0 * 0.5 * (mc + m1) * r / h2;
+        c.axzm = 0.0;
+        c.azzp = 2.0 * 0.5 * (pc + p1) * r / h2;
+        c.azzm = 0.0;
+        c.lx = lc * r / (2.0 * h2);
+        c.mxp = m1 * r / (2.0 * h2);
+        c.mxm = mc * r / (2.0 * h2);
+        c.mz = mc * r / (2.0 * h2);
+        c.lzp = l1 * r / (2.0 * h2);
+        c.lzm = lc * r / (2.0 * h2);
+    } else {
+        const double ls = lam(j + 1), ms = mu(j + 1), ps = ls + 2.0 * ms;
+        const double ln = lam(j - 1), mn = mu(j - 1), pn = ln + 2.0 * mn;
+        c.axzp = 0.5 * (mc + ms) * r / h2;
+        c.axzm = 0.5 * (mn + mc) * r / h2;
+        c.azzp = 0.5 * (pc + ps) * r / h2;
+        c.azzm = 0.5 * (pn + pc) * r / h2;
+        c.lx = lc * r / (4.0 * h2);
+        c.mxp = ms * r / (4.0 * h2);
+        c.mxm = mn * r / (4.0 * h2);
+        c.mz = mc * r / (4.0 * h2);
+        c.lzp = ls * r / (4.0 * h2);
+        c.lzm = ln * r / (4.0 * h2);
+    }
+    RowCoef<real> o;
+    o.axx = (real)c.axx; o.azx = (real)c.azx; o.axzp = (real)c.axzp; o.axzm = (real)c.axzm;
+    o.azzp = (real)c.azzp; o.azzm = (real)c.azzm; o.lx = (real)c.lx; o.mxp = (real)c.mxp;
+    o.mxm = (real)c.mxm; o.mz = (real)c.mz; o.lzp = (real)c.lzp; o.lzm = (real)c.lzm;
+    o.rf = (real)c.rf; o.cp = (real)c.cp; o.cs = (real)c.cs; o.pad = (real)0;
+    rows[j] = o;
+}
+
+void launch_rows(oed_ctx *ctx, cudaStream_t s)
+{
+    const int nl = (int)ctx->z_top.size();
+    std::vector<double> lay(4 * nl);
+    for (int l = 0; l < nl; l++) {
+        lay[l] = ctx->z_top[l];
+        lay[nl + l] = ctx->vp[l];
+        lay[2 * nl + l] = ctx->vs[l];
+        lay[3 * nl + l] = ctx->rho[l];
+    }
+    double *d_lay = nullptr;
+    cudaMalloc(&d_lay, sizeof(double) * lay.size());
+    cudaMemcpy(d_lay, lay.data(), sizeof(double) * lay.size(), cudaMemcpyHostToDevice);
+    const int nb = (ctx->g.nz + 127) / 128;
+    if (ctx->precision == OED_FP64)
+        k_rows<double><<<nb, 128, 0, s>>>(ctx->g, nl, d_lay, (RowCoef<double> *)ctx->d_rows);
+    else
+        k_rows<float><<<nb, 128, 0, s>>>(ctx->g, nl, d_lay, (RowCoef<float> *)ctx->d_rows);
+    cudaStreamSynchronize(s);
+    cudaFree(d_lay);
+}
+
+void launch_sources(const oed_ctx *ctx, const double *theta_nodes, int nnode, int per_node,
+                    const double *step, cudaStream_t s)
+{
+    FdStep st;
+    for (int j = 0; j < kNT; j++) st.d[j] = step ? step[j] : 0.0;
+    const int nsolve = nnode * per_node;
+    if (nsolve <= 0) return;
+    if (ctx->precision == OED_FP64)
+        k_sources<double><<<nsolve, 128, 0, s>>>(
+            theta_nodes, nsolve, per_node, st, ctx->g, (const RowCoef<double> *)ctx->d_rows,
+            (SourceDesc<double> *)ctx->d_src, (double *)ctx->d_stf, ctx->d_theta);
+    else
+        k_sources<float><<<nsolve, 128, 0, s>>>(
+            theta_nodes, nsolve, per_node, st, ctx->g, (const RowCoef<float> *)ctx->d_rows,
+            (SourceDesc<float> *)ctx->d_src, (float *)ctx->d_stf, ctx->d_theta);
+}
+
+}  // namespace oed

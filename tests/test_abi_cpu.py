@@ -1,0 +1,99 @@
+"""The C ABI library loads on a machine without a GPU, exports every symbol that
+include/oed.h declares, and its host-only entry points behave (no kernel runs)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1502_07873_gb300 as P
+    return P
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "oed.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(oed_[a-z_]+)\s*\(", src)))
+
+
+def test_header_symbols_exported(P):
+    L = P.library()
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(P.SYMBOLS)
+
+
+def test_status_strings(P):
+    L = P.library()
+    assert L.oed_status_string(0) == b"OED_OK"
+    assert L.oed_status_string(3) == b"OED_ENOTPD"
+    assert L.oed_status_string(99) == b"unknown"
+
+
+def test_workspace_bytes(P):
+    w = W.batched()
+    p = P.problem_from_workload(w, P.OED_FP32)
+    b = P.oed_workspace_bytes(p, 3840)
+    xp = 416
+    field = 3840 * 2 * w.nz * xp * 4
+    assert 2 * field < b < 2 * field * 1.3
+    p64 = P.problem_from_workload(w, P.OED_FP64)
+    assert P.oed_workspace_bytes(p64, 3840) > 1.9 * b
+    bad = P.make_problem(4, 4, 1.0, 1e-3, 10, W.HOMOGENEOUS, [0])
+    assert P.oed_workspace_bytes(bad, 100) == 0
+    bad2 = P.problem_from_workload(w, P.OED_FP32, rec_ix=[w.nx])
+    assert P.oed_workspace_bytes(bad2, 100) == 0
+
+
+def test_create_rejects_bad_problem_without_touching_the_device(P):
+    L = P.library()
+    h = ctypes.c_void_p()
+    bad = P.make_problem(401, 201, -5.0, 1e-3, 10, W.HOMOGENEOUS, [3])
+    assert L.oed_create(ctypes.byref(h), ctypes.byref(bad), 100) == P.OED_EINVAL
+    assert not h.value
+    assert L.oed_destroy(None) == P.OED_OK
+
+
+@pytest.mark.parametrize("dim,level", [(3, 5), (7, 3), (2, 9), (7, 5)])
+def test_smolyak_host_matches_oracle(P, oracle, dim, level):
+    x, w = P.oed_nodes_smolyak(dim, level)
+    xo, wo = oracle.smolyak(dim, level)
+    assert x.shape == xo.shape
+    assert np.max(np.abs(x - xo)) < 1e-13
+    assert np.max(np.abs(w - wo)) < 1e-11
+    lo = np.array(W.PRIOR_LO)[:dim]
+    hi = np.array(W.PRIOR_HI)[:dim]
+    xm, wm = P.oed_nodes_smolyak(dim, level, lo, hi)
+    assert np.allclose(xm, lo + (hi - lo) * (xo + 1) / 2, rtol=1e-13)
+
+
+def test_smolyak_host_rejects_small_buffer(P):
+    L = P.library()
+    cnt = ctypes.c_int()
+    x = np.zeros((10, 7))
+    wt = np.zeros(10)
+    rc = L.oed_nodes_smolyak(7, 3, None, None, 10, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             wt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cnt))
+    assert rc == P.OED_ENOMEM and cnt.value == 589
+
+
+def test_product_path_has_no_oracle_import():
+    """The package must not reach the oracle (or any CPU fallback)."""
+    pkg = os.path.join(ROOT, "paper_1502_07873_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in txt.replace("the oracle", ""), f

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+  - FP64 stencil: seismograms normwise max|g - g_ref| / max|g_ref| <= 1e-10, scaled
+    Hessian entries |H - H_ref|_ij / sqrt(H_ii H_jj) <= 1e-9, EIG relative <= 1e-9.
+  - FP32 stencil (FP64 Jacobian / Hessian / log-det): seismograms <= 1e-4, EIG
+    relative <= 1e-3.
+Sizes span several 32-column tiles and 8-row segments with ragged tails.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1502_07873_gb300 as P
+    return P
+
+
+def _t(a, dtype=torch.float64):
+    return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+def _normwise(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _scaled(H, Href):
+    d = np.sqrt(np.abs(np.einsum("...ii->...i", Href)))
+    return float(np.max(np.abs(H - Href) / (d[..., :, None] * d[..., None, :])))
+
+
+GRIDS = {
+    "homog_75x37": dict(nx=75, nz=37, h=27.0, nsteps=150, nrec=4),
+    "layered_70x41": dict(nx=70, nz=41, h=25.0, nsteps=140, nrec=5,
+                          layers=((0.0, 2000.0, 1155.0, 2200.0), (300.0, 3000.0, 1732.0, 2500.0),
+                                  (600.0, 4500.0, 2598.0, 2700.0))),
+}
+
+
+def _thetas(w, n, seed=5):
+    rng = np.random.default_rng(seed)
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+    return lo + (hi - lo) * rng.random((n, 7))
+
+
+@pytest.mark.parametrize("grid", sorted(GRIDS))
+@pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-4)])
+def test_forward_matches_oracle(P, oracle, grid, prec, tol):
+    w = W.tiny(**GRIDS[grid])
+    th = _thetas(w, 5)
+    G = oracle.Grid.from_workload(w)
+    ref = np.stack([oracle.forward(G, t) for t in th])
+    ctx = P.Context(P.problem_from_workload(w, prec), max_solves=15)
+    g = torch.empty((5, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
+    P.oed_forward(ctx, _t(th), g)
+    torch.cuda.synchronize()
+    out = g.cpu().numpy()
+    for s in range(5):
+        assert _normwise(out[s], ref[s]) <= tol, (s, _normwise(out[s], ref[s]))
+
+
+def test_forward_chunks_and_empty(P, oracle):
+    """n > max_solves runs in chunks (15, 15, 7); n = 0 is a no-op."""
+    w = W.tiny(nx=41, nz=21, nsteps=60, nrec=3)
+    th = _thetas(w, 37, seed=9)
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP64), max_solves=15)
+    g = torch.empty((37, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
+    P.oed_forward(ctx, _t(th), g)
+    P.oed_forward(ctx, _t(np.zeros((0, 7))), torch.empty((0, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    G = oracle.Grid.from_workload(w)
+    for s in (0, 14, 15, 29, 30, 36):
+        assert _normwise(g[s].cpu().numpy(), oracle.forward(G, th[s])) <= 1e-10
+
+
+def test_forward_invalid_source_is_nan(P):
+    w = W.tiny(nx=41, nz=21, nsteps=20, nrec=3)
+    th = _thetas(w, 2)
+    th[1, 0] = 10.0   # patch leaves the grid
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=15)
+    g = torch.empty((2, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
+    P.oed_forward(ctx, _t(th), g)
+    out = g.cpu().numpy()
+    assert np.all(np.isfinite(out[0])) and np.all(np.isnan(out[1]))
+
+
+@pytest.mark.parametrize("grid", sorted(GRIDS))
+def test_hessian_fp64_matches_oracle(P, oracle, grid):
+    w = W.tiny(**GRIDS[grid])
+    th = _thetas(w, 3, seed=2)
+    wl = [31, 77, w.nlevels]
+    G = oracle.Grid.from_workload(w)
+    sigma = 0.07
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP64), max_solves=30)   # chunks of 2 nodes
+    H = torch.empty((3, 7, 7), dtype=torch.float64, device=DEV)
+    Hr = torch.empty((3, w.nrec, 3, 28), dtype=torch.float64, device=DEV)
+    st = torch.full((3,), -1, dtype=torch.int32, device=DEV)
+    P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, sigma, H, win_levels=wl,
+                  H_rec=Hr, status=st)
+    torch.cuda.synchronize()
+    iu = np.triu_indices(7)
+    for i in range(3):
+        Href, Hrref = oracle.node_hessian(G, th[i], w.prior_lo, w.prior_hi, w.rel_step, sigma, wl)
+        assert _scaled(H[i].cpu().numpy(), Href) <= 1e-9
+        for r in range(w.nrec):
+            for k in range(3):
+                ref_u = Hrref[r, k][iu]
+                dd = np.sqrt(np.outer(np.diag(Href), np.diag(Href)))[iu]
+                assert np.max(np.abs(Hr[i, r, k].cpu().numpy() - ref_u) / dd) <= 1e-9
+    assert st.cpu().numpy().tolist() == [0, 0, 0]
+
+
+def test_eig_plain_small_fp64_and_fp32(P, oracle):
+    """The 81x41 / 400-step / 16-node workload end to end: FP64 to 1e-9, FP32 to 1e-3."""
+    w = W.plain_small()
+    G = oracle.Grid.from_workload(w)
+    th, wt = oracle.mc_nodes(w.uniforms(), w.prior_lo, w.prior_hi)
+    sigma = 0.4
+    ref = oracle.eig(G, th, wt, w.prior_lo, w.prior_hi, w.rel_step, sigma, want_h=True)
+    for prec, tol in ((P.OED_FP64, 1e-9), (P.OED_FP32, 1e-3)):
+        ctx = P.Context(P.problem_from_workload(w, prec), max_solves=240)
+        H = torch.empty((16, 7, 7), dtype=torch.float64, device=DEV)
+        P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, sigma, H)
+        eig = torch.empty(1, dtype=torch.float64, device=DEV)
+        dkl = torch.empty(16, dtype=torch.float64, device=DEV)
+        nb = torch.empty(1, dtype=torch.int32, device=DEV)
+        P.oed_eig(ctx, H, _t(wt), w.prior_lo, w.prior_hi, eig, dkl=dkl, n_bad=nb)
+        torch.cuda.synchronize()
+        assert int(nb.item()) == 0
+        e = float(eig.item())
+        assert abs(e - ref["eig"]) / abs(ref["eig"]) <= tol, (prec, e, ref["eig"])
+        assert np.max(np.abs(dkl.cpu().numpy() - ref["dkl"]) / np.abs(ref["dkl"])) <= tol * 10
+        if prec == P.OED_FP64:
+            assert _scaled(H.cpu().numpy(), ref["H"]) <= 1e-9
+
+
+def test_chunking_is_bitwise_invariant(P):
+    w = W.tiny(nx=41, nz=21, nsteps=50, nrec=3)
+    th = _thetas(w, 7, seed=3)
+    out = []
+    for ms in (45, 150):
+        ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=ms)
+        H = torch.empty((7, 7, 7), dtype=torch.float64, device=DEV)
+        P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, 0.1, H)
+        out.append(H.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_status_invalid_source_and_not_pd(P):
+    w = W.tiny(nx=41, nz=21, nsteps=40, nrec=3)
+    th = _thetas(w, 3, seed=4)
+    th[1, 1] = 5.0   # depth 5 m: the 6x6 patch leaves the grid through the surface
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=45)
+    H = torch.empty((3, 7, 7), dtype=torch.float64, device=DEV)
+    st = torch.empty(3, dtype=torch.int32, device=DEV)
+    P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, 0.1, H, status=st)
+    assert st.cpu().tolist() == [0, P.OED_EINVAL, 0]
+    assert torch.isnan(H[1]).all()
+    # an indefinite matrix is flagged, excluded from the sum and counted
+    H[2] = torch.eye(7, dtype=torch.float64, device=DEV)
+    H[2, 2, 3] = H[2, 3, 2] = 1.5
+    eig = torch.empty(1, dtype=torch.float64, device=DEV)
+    s2 = torch.empty(3, dtype=torch.int32, device=DEV)
+    nb = torch.empty(1, dtype=torch.int32, device=DEV)
+    dkl = torch.empty(3, dtype=torch.float64, device=DEV)
+    wt = _t([0.25, 0.25, 0.5])
+    P.oed_eig(ctx, H, wt, w.prior_lo, w.prior_hi, eig, dkl=dkl, status=s2, n_bad=nb)
+    assert s2.cpu().tolist() == [0, P.OED_ENOTPD, P.OED_ENOTPD]
+    assert int(nb.item()) == 2
+    assert abs(float(eig.item()) - 0.25 * float(dkl[0].item())) < 1e-12 * abs(float(eig.item()))
+
+
+def test_designs_match_oracle(P, oracle):
+    """EIG of receiver subsets from per-receiver, per-window partial Hessians."""
+    w = W.tiny(nx=61, nz=25, h=33.0, nsteps=90, nrec=6, win_seconds=None)
+    th = _thetas(w, 4, seed=8)
+    wt = np.array([0.1, 0.2, 0.3, 0.4])
+    wl = [46, w.nlevels]
+    sigma = 0.05
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP64), max_solves=60)
+    H = torch.empty((4, 7, 7), dtype=torch.float64, device=DEV)
+    Hr = torch.empty((4, w.nrec, 2, 28), dtype=torch.float64, device=DEV)
+    P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, sigma, H, win_levels=wl, H_rec=Hr)
+    rng = np.random.default_rng(0)
+    masks = (rng.random((9, w.nrec)) < 0.5).astype(np.uint8)
+    masks[0] = 1
+    masks[1] = 0
+    masks[1, 2] = 1
+    G = oracle.Grid.from_workload(w)
+    refs = [oracle.node_hessian(G, t, w.prior_lo, w.prior_hi, w.rel_step, sigma, wl)[1] for t in th]
+    lp = oracle.log_uniform_density(w.prior_lo, w.prior_hi)
+    for win in (0, 1):
+        eig = torch.empty(9, dtype=torch.float64, device=DEV)
+        nb = torch.empty(9, dtype=torch.int32, device=DEV)
+        P.oed_eig_designs(ctx, Hr, win, _t(masks, torch.uint8), _t(wt), w.prior_lo, w.prior_hi, eig, n_bad=nb)
+        e = eig.cpu().numpy()
+        bad = nb.cpu().numpy()
+        for d in range(9):
+            sel = np.nonzero(masks[d])[0]
+            tot, nbad = 0.0, 0
+            for i in range(4):
+                Hd = sum(refs[i][r, win] for r in sel) if len(sel) else np.zeros((7, 7))
+                ld, _, ok = oracle.scaled_logdet(Hd)
+                if ok:
+                    tot += wt[i] * oracle.dkl(ld, 7, lp)
+                else:
+                    nbad += 1
+            assert bad[d] == nbad
+            if nbad == 0:
+                assert abs(e[d] - tot) <= 1e-9 * abs(tot), (win, d, e[d], tot)
+    # all receivers over the full window equals the plain EIG
+    e_all = torch.empty(1, dtype=torch.float64, device=DEV)
+    P.oed_eig(ctx, H, _t(wt), w.prior_lo, w.prior_hi, e_all)
+    eig = torch.empty(9, dtype=torch.float64, device=DEV)
+    P.oed_eig_designs(ctx, Hr, 1, _t(masks, torch.uint8), _t(wt), w.prior_lo, w.prior_hi, eig)
+    assert abs(float(eig[0].item()) - float(e_all.item())) <= 1e-10 * abs(float(e_all.item()))
+
+
+def test_eig_host_matches_device_path(P, oracle):
+    w = W.tiny(nx=41, nz=21, nsteps=60, nrec=4, n_nodes=5)
+    th, wt = oracle.mc_nodes(w.uniforms(), w.prior_lo, w.prior_hi)
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=45)
+    e_host, dkl, nb = P.oed_eig_host(ctx, th, wt, w.prior_lo, w.prior_hi, w.rel_step, 0.1, want_dkl=True)
+    H = torch.empty((5, 7, 7), dtype=torch.float64, device=DEV)
+    P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, 0.1, H)
+    eig = torch.empty(1, dtype=torch.float64, device=DEV)
+    P.oed_eig(ctx, H, _t(wt), w.prior_lo, w.prior_hi, eig)
+    assert nb == 0
+    assert e_host == float(eig.item())
+
+
+def test_nodes_mc_matches_oracle(P, oracle):
+    w = W.batched()
+    u = w.uniforms()
+    th = torch.empty((u.shape[0], 7), dtype=torch.float64, device=DEV)
+    wt = torch.empty(u.shape[0], dtype=torch.float64, device=DEV)
+    P.oed_nodes_mc(_t(u), w.prior_lo, w.prior_hi, th, wt)
+    rt, rw = oracle.mc_nodes(u, w.prior_lo, w.prior_hi)
+    assert np.allclose(th.cpu().numpy(), rt, rtol=1e-15, atol=0)
+    assert np.allclose(wt.cpu().numpy(), rw, rtol=1e-15, atol=0)
+
+
+@pytest.mark.slow
+def test_full_size_batched_sampled(P, oracle):
+    """401x201 grid, 2000 steps, 256 nodes x 15 solves in one launch configuration (the
+    benchmark's): sampled seismograms and a sampled node's gain against the oracle."""
+    w = W.batched()
+    th, wt = oracle.mc_nodes(w.uniforms(), w.prior_lo, w.prior_hi)
+    sigma = 0.5
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=3840)
+    H = torch.empty((256, 7, 7), dtype=torch.float64, device=DEV)
+    P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, sigma, H)
+    dkl = torch.empty(256, dtype=torch.float64, device=DEV)
+    eig = torch.empty(1, dtype=torch.float64, device=DEV)
+    nb = torch.empty(1, dtype=torch.int32, device=DEV)
+    P.oed_eig(ctx, H, _t(wt), w.prior_lo, w.prior_hi, eig, dkl=dkl, n_bad=nb)
+    torch.cuda.synchronize()
+    assert int(nb.item()) == 0
+    G = oracle.Grid.from_workload(w)
+    lp = oracle.log_uniform_density(w.prior_lo, w.prior_hi)
+    for i in (0, 137):
+        Href, _ = oracle.node_hessian(G, th[i], w.prior_lo, w.prior_hi, w.rel_step, sigma)
+        ld, _, ok = oracle.scaled_logdet(Href)
+        d_ref = oracle.dkl(ld, 7, lp)
+        assert abs(float(dkl[i].item()) - d_ref) <= 1e-3 * abs(d_ref), (i, float(dkl[i].item()), d_ref)
+    # seismograms of two solves of the same launch shape
+    g = torch.empty((2, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
+    P.oed_forward(ctx, _t(th[[5, 200]]), g)
+    for k, i in enumerate((5, 200)):
+        assert _normwise(g[k].cpu().numpy(), oracle.forward(G, th[i])) <= 1e-4
