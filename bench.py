@@ -239,6 +239,7 @@ def run_ours(args, rank, world, local):
     eig = torch.empty(1, dtype=torch.float64, device=dev)
     nbad = torch.empty(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tuning = ctx.autotune(nsolve, stream=stream)   # launch shape of the stencil, set once
 
     def step():
         P.oed_hessian(ctx, theta, w.prior_lo, w.prior_hi, w.rel_step, sigma, H, stream=stream)
@@ -323,6 +324,8 @@ def run_ours(args, rank, world, local):
                    "nodes_per_gpu": w.n_nodes, "solves_per_gpu": nsolve, "receivers": w.nrec,
                    "precision": f"{args.precision} stencil; f64 jacobian, hessian, log-det, sum",
                    "parallelism": f"replicas x{world} (independent node batches)",
+                   "stencil_kernel": ("cluster-resident, %d CTAs per solve" % tuning[0]) if tuning[0]
+                   else "streaming, %d rows/thread, %d warps/block" % (tuning[1], tuning[2]),
                    "l2": "no flush: 5.1 GB of wavefields per step exceed the 129 MB L2"},
         "gcell_upd_per_s": world * cells * args.steps / (total_ms * 1e-3) / 1e9,
         "stencil_gcell_upd_per_s": per_launch_cells / (st_ms * 1e-3) / 1e9,

@@ -65,7 +65,7 @@ typedef struct {
     const double *z_top; /* [nlayers] layer tops, z_top[0] = 0, increasing; a node on
                             an interface belongs to the deeper layer */
     const double *vp, *vs, *rho; /* [nlayers] P and S speed (m/s), density (kg/m^3) */
-    int nrec;          /* receivers, 1..256 */
+    int nrec;          /* receivers, 1..4096 (oed_hessian accepts at most 256) */
     const int *rec_ix; /* [nrec] surface node index i of each receiver (0 <= i < nx);
                           repeats allowed */
     int precision;     /* OED_FP32 or OED_FP64 */
@@ -97,6 +97,30 @@ const char *oed_status_string(int status);
  *   ms        host [1] milliseconds
  *   launches  host [1] or NULL: stencil launches in that interval (0 if none yet) */
 int oed_last_step_time(const oed_ctx *ctx, float *ms, int *launches);
+
+/* Time stepping runs in one of two kernels:
+ *  - streaming: one launch per step over all solves, wavefields in HBM
+ *    (any grid, FP32 or FP64), replayed from a captured CUDA graph;
+ *  - cluster-resident (FP32, grids whose two time levels fit in the shared
+ *    memory of a cluster of C <= 8 CTAs, e.g. 401x201): one launch for all
+ *    steps, one thread-block cluster per solve, wavefield kept on chip.
+ * Both give the same node updates.  oed_autotune times every streaming launch
+ * shape (rows marched per thread 2/4/8 x warps per block 1/2/4/8) and every
+ * feasible cluster size on nsolve solves of this context's grid, keeps the
+ * fastest for later calls, and synchronises the stream.  It overwrites the
+ * context's workspace (no caller data).  nsolve in 1..max_solves, typically
+ * 15 * oed_chunk_nodes(ctx). */
+int oed_autotune(oed_ctx *ctx, int nsolve, void *stream);
+
+/* Current / forced choice: cluster_size 0 = streaming kernel with the given
+ * rows_per_thread (2, 4, 8) and warps_per_block (1, 2, 4, 8); cluster_size > 0 =
+ * cluster-resident kernel (OED_EINVAL if the grid does not fit). */
+int oed_get_tuning(const oed_ctx *ctx, int *cluster_size, int *rows_per_thread,
+                   int *warps_per_block);
+int oed_set_tuning(oed_ctx *ctx, int cluster_size, int rows_per_thread, int warps_per_block);
+
+/* Smallest cluster size of the resident kernel for this context, 0 if none. */
+int oed_resident_min_cluster(const oed_ctx *ctx);
 
 /* Largest node chunk oed_hessian processes per pass (max_solves / 15). */
 int oed_chunk_nodes(const oed_ctx *ctx);

@@ -25,7 +25,8 @@ NTHETA = 7
 SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_status_string", "oed_chunk_nodes", "oed_forward", "oed_hessian", "oed_eig",
            "oed_eig_designs", "oed_nodes_mc", "oed_nodes_smolyak", "oed_eig_host",
-           "oed_last_step_time")
+           "oed_last_step_time", "oed_autotune", "oed_get_tuning", "oed_set_tuning",
+           "oed_resident_min_cluster")
 
 
 class OedError(RuntimeError):
@@ -72,6 +73,10 @@ def library():
         "oed_nodes_smolyak": (i, [i, i, dp, dp, i, dp, dp, ip]),
         "oed_eig_host": (i, [vp, dp, dp, i, dp, dp, d, d, dp, dp, ip]),
         "oed_last_step_time": (i, [vp, ctypes.POINTER(ctypes.c_float), ip]),
+        "oed_autotune": (i, [vp, i, vp]),
+        "oed_get_tuning": (i, [vp, ip, ip, ip]),
+        "oed_set_tuning": (i, [vp, i, i, i]),
+        "oed_resident_min_cluster": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -180,6 +185,27 @@ class Context:
         _check(self.handle, library().oed_last_step_time(self.handle, ctypes.byref(ms), ctypes.byref(n)),
                "oed_last_step_time")
         return float(ms.value), int(n.value)
+
+    def autotune(self, nsolve: Optional[int] = None, stream=None):
+        """Pick the fastest stencil launch shape for nsolve solves (default: a full chunk)."""
+        n = nsolve or 15 * self.chunk_nodes
+        _check(self.handle, library().oed_autotune(self.handle, int(n), _stream(stream)), "oed_autotune")
+        return self.tuning
+
+    @property
+    def tuning(self):
+        """(cluster_size, rows_per_thread, warps_per_block); cluster_size 0 = streaming kernel."""
+        c, zs, wz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        library().oed_get_tuning(self.handle, ctypes.byref(c), ctypes.byref(zs), ctypes.byref(wz))
+        return int(c.value), int(zs.value), int(wz.value)
+
+    def set_tuning(self, cluster_size: int = 0, rows_per_thread: int = 4, warps_per_block: int = 4):
+        _check(self.handle, library().oed_set_tuning(self.handle, int(cluster_size), int(rows_per_thread),
+                                                      int(warps_per_block)), "oed_set_tuning")
+
+    @property
+    def resident_min_cluster(self) -> int:
+        return int(library().oed_resident_min_cluster(self.handle))
 
     @property
     def chunk_nodes(self) -> int:

@@ -50,7 +50,7 @@ static bool problem_ok(const oed_problem *p, std::string *why)
         if (!(p->vp[l] * p->vp[l] >= 2.0 * p->vs[l] * p->vs[l]))
             return fail("vp^2 >= 2 vs^2 required (lambda >= 0)");
     }
-    if (p->nrec < 1 || p->nrec > kMaxRec || !p->rec_ix) return fail("nrec must be in 1..256");
+    if (p->nrec < 1 || p->nrec > kMaxRec || !p->rec_ix) return fail("nrec must be in 1..4096");
     for (int r = 0; r < p->nrec; r++)
         if (p->rec_ix[r] < 0 || p->rec_ix[r] >= p->nx) return fail("receiver index outside 0..nx-1");
     if (p->precision != OED_FP32 && p->precision != OED_FP64) return fail("precision must be OED_FP32 or OED_FP64");
@@ -106,6 +106,13 @@ static void drop_graphs(oed_ctx *ctx)
 // (built on first use for this batch size).
 static int run_steps(oed_ctx *ctx, int nsolve, cudaStream_t st)
 {
+    if (ctx->tune.C > 0) {
+        // one persistent launch integrates every step; no wavefield in HBM
+        ctx->last_steps_launches = ctx->g.nsteps;
+        return cuda_err(ctx, launch_resident(ctx, ctx->tune.C, nsolve, st, ctx->ev_steps[0],
+                                             ctx->ev_steps[1], 0),
+                        "cluster-resident launch");
+    }
     auto it = ctx->graphs.find(nsolve);
     if (it == ctx->graphs.end()) {
         cudaStream_t cap;
@@ -210,6 +217,7 @@ int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
     ctx->d_rows = q; q += s.rows;
     ctx->d_rec = (int *)q; q += s.rec;
     ctx->d_hseg = (double *)q; q += s.hseg;
+    cudaMemset(ctx->d_src, 0, s.src);   // defined descriptors before the first source setup
     cudaMemcpy(ctx->d_rec, ctx->rec_ix.data(), sizeof(int) * p->nrec, cudaMemcpyHostToDevice);
     cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
     cudaEventCreate(&ctx->ev_steps[0]);
@@ -257,7 +265,106 @@ int oed_last_step_time(const oed_ctx *ctx, float *ms, int *launches)
     if (launches) *launches = ctx->last_steps_launches;
     if (!ctx->last_steps_launches) return OED_OK;
     cudaError_t e = cudaEventElapsedTime(ms, ctx->ev_steps[0], ctx->ev_steps[1]);
-    return e == cudaSuccess ? OED_OK : OED_ECUDA;
+    if (e != cudaSuccess) {
+        const_cast<oed_ctx *>(ctx)->err = std::string("oed_last_step_time: ") + cudaGetErrorString(e);
+        return OED_ECUDA;
+    }
+    return OED_OK;
+}
+
+int oed_autotune(oed_ctx *ctx, int nsolve, void *stream)
+{
+    if (!ctx || nsolve < 1 || nsolve > ctx->max_solves)
+        return set_err(ctx, OED_EINVAL, "oed_autotune: nsolve must be in 1..max_solves");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // streaming kernel: enough launches for ~20 ms per candidate, at least 4
+    const double cells = (double)nsolve * ctx->g.nx * ctx->g.nz;
+    int nrep = (int)(2e9 / (cells * ctx->elem * 6 + 1.0));
+    nrep = nrep < 4 ? 4 : (nrep > 200 ? 200 : nrep);
+    const StepTuning keep = ctx->tune;
+    StepTuning best = keep;
+    float best_ms = 1e30f;   // per time step
+    auto fail = [&](cudaError_t e) {
+        ctx->tune = keep;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_err(ctx, e, "oed_autotune");
+    };
+    const int zs_list[] = {2, 4, 8};
+    const int wz_list[] = {1, 2, 4, 8};
+    for (int zs : zs_list)
+        for (int wz : wz_list) {
+            ctx->tune = StepTuning{zs, wz, 0};
+            launch_step_probe(ctx, nsolve, 2, st, e0, e1);   // warm
+            launch_step_probe(ctx, nsolve, nrep, st, e0, e1);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) return fail(e);
+            ms /= nrep;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = ctx->tune;
+            }
+        }
+    // cluster-resident kernel (FP32 grids whose two levels fit in 1..8 CTAs)
+    const int cmin = resident_cluster_size(ctx);
+    if (cmin > 0) {
+        const int probe_steps = ctx->g.nsteps < 64 ? ctx->g.nsteps : 64;
+        for (int C = cmin; C <= 8; C++) {
+            if (resident_max_active_clusters(ctx, C) < 1) continue;
+            ctx->tune = StepTuning{best.zs, best.wz, C};
+            cudaError_t e = launch_resident(ctx, C, nsolve, st, e0, e1, probe_steps);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) return fail(e);
+            ms /= probe_steps;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = ctx->tune;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune = best;
+    drop_graphs(ctx);   // captured loops used the previous shape
+    return OED_OK;
+}
+
+int oed_get_tuning(const oed_ctx *ctx, int *cluster_size, int *rows_per_thread, int *warps_per_block)
+{
+    if (!ctx) return OED_EINVAL;
+    if (cluster_size) *cluster_size = ctx->tune.C;
+    if (rows_per_thread) *rows_per_thread = ctx->tune.zs;
+    if (warps_per_block) *warps_per_block = ctx->tune.wz;
+    return OED_OK;
+}
+
+int oed_set_tuning(oed_ctx *ctx, int cluster_size, int rows_per_thread, int warps_per_block)
+{
+    if (!ctx) return OED_EINVAL;
+    if ((rows_per_thread != 2 && rows_per_thread != 4 && rows_per_thread != 8) ||
+        (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8))
+        return set_err(ctx, OED_EINVAL, "oed_set_tuning: rows 2/4/8, warps 1/2/4/8");
+    if (cluster_size != 0) {
+        const int cmin = resident_cluster_size(ctx);
+        if (cmin == 0 || cluster_size < cmin || cluster_size > 8 ||
+            resident_max_active_clusters(ctx, cluster_size) < 1)
+            return set_err(ctx, OED_EINVAL, "oed_set_tuning: the grid does not fit that cluster");
+    }
+    ctx->tune = StepTuning{rows_per_thread, warps_per_block, cluster_size};
+    drop_graphs(ctx);
+    return OED_OK;
+}
+
+int oed_resident_min_cluster(const oed_ctx *ctx)
+{
+    return ctx ? resident_cluster_size(ctx) : 0;
 }
 
 int oed_chunk_nodes(const oed_ctx *ctx)
@@ -290,6 +397,8 @@ int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, cons
         return set_err(ctx, OED_EINVAL, "oed_hessian: bad pointer arguments");
     if (!(rel_step > 0) || !(sigma > 0) || !std::isfinite(rel_step) || !std::isfinite(sigma))
         return set_err(ctx, OED_EINVAL, "oed_hessian: rel_step and sigma must be positive");
+    if (ctx->g.nrec > kMaxRecHessian)
+        return set_err(ctx, OED_EINVAL, "oed_hessian: at most 256 receivers");
     if (nwin < 0 || nwin > 15 || (nwin > 0 && !win_levels) || (H_rec && nwin == 0))
         return set_err(ctx, OED_EINVAL, "oed_hessian: 0..15 windows; H_rec needs windows");
     double inv2d[kNT], d[kNT];
@@ -346,7 +455,7 @@ int oed_eig_designs(oed_ctx *ctx, const double *H_rec, int n, int nrec, int nwin
                     const unsigned char *mask, int ndesign, const double *w, const double *lo,
                     const double *hi, double *eig, int *n_bad, void *stream)
 {
-    if (n < 0 || nrec < 1 || nrec > kMaxRec || nwin < 1 || win < 0 || win >= nwin || ndesign < 0 ||
+    if (n < 0 || nrec < 1 || nrec > kMaxRecHessian || nwin < 1 || win < 0 || win >= nwin || ndesign < 0 ||
         (n > 0 && (!H_rec || !w)) || (ndesign > 0 && (!mask || !eig)) || !lo || !hi)
         return set_err(ctx, OED_EINVAL, "oed_eig_designs: bad arguments");
     for (int j = 0; j < kNT; j++)

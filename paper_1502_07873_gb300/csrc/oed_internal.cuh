@@ -17,7 +17,8 @@ namespace oed {
 
 constexpr int kNT = 7;    // source parameters
 constexpr int kNP = 15;   // solves per node: centre and +/- d_j e_j
-constexpr int kMaxRec = 256;
+constexpr int kMaxRec = 4096;      // receivers of a forward solve
+constexpr int kMaxRecHessian = 256; // receivers of oed_hessian / oed_eig_designs
 
 // Per-row stencil coefficients of the leap-frog update (Eq. Full_Disc) for a
 // medium that is constant along each grid row (layered in depth).  Every
@@ -36,7 +37,7 @@ constexpr int kMaxRec = 256;
 //   rf = dt^2/nu_j multiplies the force density; cp, cs = c dt / h for the
 //   absorbing rows (side columns of this row; the whole bottom row).
 template <typename real>
-struct RowCoef {
+struct __align__(16 * sizeof(real)) RowCoef {
     real axx, azx, axzp, axzm, azzp, azzm, lx, mxp, mxm, mz, lzp, lzm, rf, cp, cs, pad;
 };
 
@@ -60,8 +61,9 @@ struct Geometry {
 };
 
 struct StepTuning {
-    int zs;      // rows marched per thread
-    int wz;      // warps along z in a block
+    int zs;      // streaming kernel: rows marched per thread
+    int wz;      // streaming kernel: warps along z in a block
+    int C;       // > 0: cluster-resident kernel with clusters of C CTAs (FP32 only)
 };
 
 }  // namespace oed
@@ -86,7 +88,7 @@ struct oed_ctx {
     double *d_hseg = nullptr;  // [chunk][nrec][nseg_max][28] partial Hessians
     int nseg_max = 0;
     size_t bytes = 0;
-    oed::StepTuning tune{8, 4};
+    oed::StepTuning tune{4, 4, 0};
     // host-path staging
     cudaStream_t own_stream = nullptr;
     double *h_stage_theta = nullptr, *h_stage_w = nullptr, *h_stage_H = nullptr,
@@ -113,6 +115,14 @@ void launch_rows(oed_ctx *ctx, cudaStream_t s);
 void launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t s, cudaEvent_t ev0,
                           cudaEvent_t ev1);
 void launch_trace_to_f64(const oed_ctx *ctx, int nsolve, double *g, cudaStream_t s);
+void launch_step_probe(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st, cudaEvent_t ev0,
+                       cudaEvent_t ev1);
+
+// resident.cu
+int resident_cluster_size(const oed_ctx *ctx);
+int resident_max_active_clusters(const oed_ctx *ctx, int C);
+cudaError_t launch_resident(const oed_ctx *ctx, int C, int nsolve, cudaStream_t st, cudaEvent_t ev0,
+                            cudaEvent_t ev1, int nsteps_override);
 
 // hessian.cu
 void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double sigma,

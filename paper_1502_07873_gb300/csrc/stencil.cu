@@ -11,15 +11,17 @@
 // Memory layout: u[solve][component][z][xp] with xp a multiple of 32, so every warp
 // reads and writes whole 128-byte lines.  u^{m+1} overwrites u^{m-1} in place (each
 // node reads only its own u^{m-1}), so a solve needs two level buffers.
-// Each thread owns one column i and marches ZS rows downward, keeping a 3x3
-// register window of u_x and u_z (rows j-1, j, j+1; columns i-1, i, i+1): every
-// value of u^m is fetched from L2/HBM once and re-read from L1 by its two
-// horizontal neighbours.  HBM traffic is the algorithmic minimum: read u^m and
-// u^{m-1}, write u^{m+1}, two components each (24 B per cell-update in FP32).
+// Each thread owns one column i and ZS consecutive rows.  It issues all of its
+// loads first (rows j-1 .. j+ZS of u^m at columns i-1, i, i+1, both components,
+// and its ZS values of u^{m-1}), so each thread keeps ~8 ZS independent loads in
+// flight, then computes and stores its ZS nodes.  Horizontal neighbours are L1
+// hits and the two halo rows of a segment are L2 hits, so HBM traffic is the
+// algorithmic minimum: read u^m and u^{m-1}, write u^{m+1}, two components each
+// (24 B per cell-update in FP32).
 //
 // The same launch gathers the receiver samples of level m from its input u^m
 // (Eq. forward_model), so the seismograms need no extra pass over the field.
-#include "oed_internal.cuh"
+#include "stencil_cell.cuh"
 
 namespace oed {
 
@@ -69,74 +71,50 @@ __global__ void __launch_bounds__(256) k_step(StepArgs<real> a)
     real *__restrict__ pz = px + g.comp_stride;
     const int im = i > 0 ? i - 1 : 0;
     const int ip = i < g.nx - 1 ? i + 1 : g.nx - 1;
-    const bool left = (i == 0), right = (i == g.nx - 1);
+    const int side = (i == 0) ? 1 : ((i == g.nx - 1) ? 2 : 0);
+    const int jlast = g.nz - 1;
 
+    // Issue every load of this thread before any arithmetic: rows jb-1 .. jb+ZS of
+    // u^m (three columns, two components) and rows jb .. jb+ZS-1 of u^{m-1}.  Rows
+    // outside the grid are clamped (their values are never used).
+    real X[ZS + 2][3], Z[ZS + 2][3], XM[ZS], ZM[ZS];
+#pragma unroll
+    for (int k = 0; k < ZS + 2; k++) {
+        int j = jb - 1 + k;
+        j = j < 0 ? 0 : (j > jlast ? jlast : j);
+        const size_t o = (size_t)j * g.xp;
+        load3(cx + o, im, i, ip, X[k]);
+        load3(cz + o, im, i, ip, Z[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < ZS; k++) {
+        const int j = jb + k < jlast ? jb + k : jlast;
+        const size_t o = (size_t)j * g.xp + i;
+        XM[k] = __ldcs(px + o);   // read once, never reused: streaming
+        ZM[k] = __ldcs(pz + o);
+    }
     const int si = i - a.src[s].i0;
     const int sj = a.src[s].j0;
     const bool scol = (unsigned)si < 6u;
     const real S = scol ? a.stf[(size_t)s * g.nsteps + a.m] : (real)0;
 
-    real xn[3], xc[3], xs[3], zn[3], zc[3], zs[3];
-    {
-        const size_t on = (size_t)(jb > 0 ? jb - 1 : 0) * g.xp;
-        const size_t oc = (size_t)jb * g.xp;
-        load3(cx + on, im, i, ip, xn);
-        load3(cz + on, im, i, ip, zn);
-        load3(cx + oc, im, i, ip, xc);
-        load3(cz + oc, im, i, ip, zc);
-    }
 #pragma unroll
     for (int k = 0; k < ZS; k++) {
         const int j = jb + k;
-        if (j >= g.nz) break;
-        {
-            const size_t os = (size_t)(j < g.nz - 1 ? j + 1 : j) * g.xp;
-            load3(cx + os, im, i, ip, xs);
-            load3(cz + os, im, i, ip, zs);
-        }
-        const size_t o = (size_t)j * g.xp + i;
-        const real uxm = px[o], uzm = pz[o];
+        if (j > jlast) break;
         const RowCoef<real> R = a.rows[j];
+        const int b = j - sj;
+        real fx = (real)0, fz = (real)0;
+        if (scol && (unsigned)b < 6u) {
+            fx = S * a.src[s].wx[b * 6 + si];
+            fz = S * a.src[s].wz[b * 6 + si];
+        }
         real ux, uz;
-        if (left || right) {
-            const real xi = left ? xc[2] : xc[0];
-            const real zi = left ? zc[2] : zc[0];
-            ux = xc[1] + R.cp * (xi - xc[1]);
-            uz = zc[1] + R.cs * (zi - zc[1]);
-        } else if (j == g.nz - 1) {
-            ux = xc[1] + R.cs * (xn[1] - xc[1]);
-            uz = zc[1] + R.cp * (zn[1] - zc[1]);
-        } else {
-            real Ax = R.axx * (xc[2] - (real)2 * xc[1] + xc[0]) + R.axzp * (xs[1] - xc[1]);
-            real Az = R.azx * (zc[2] - (real)2 * zc[1] + zc[0]) + R.azzp * (zs[1] - zc[1]);
-            if (j > 0) {
-                Ax += -R.axzm * (xc[1] - xn[1]) + R.lx * ((zs[2] - zn[2]) - (zs[0] - zn[0])) +
-                      R.mxp * (zs[2] - zs[0]) - R.mxm * (zn[2] - zn[0]);
-                Az += -R.azzm * (zc[1] - zn[1]) + R.mz * ((xs[2] - xn[2]) - (xs[0] - xn[0])) +
-                      R.lzp * (xs[2] - xs[0]) - R.lzm * (xn[2] - xn[0]);
-            } else {
-                Ax += R.lx * ((zs[2] - zc[2]) - (zs[0] - zc[0])) + R.mxm * (zc[2] - zc[0]) +
-                      R.mxp * (zs[2] - zs[0]);
-                Az += R.mz * ((xs[2] - xc[2]) - (xs[0] - xc[0])) + R.lzm * (xc[2] - xc[0]) +
-                      R.lzp * (xs[2] - xs[0]);
-            }
-            const int b = j - sj;
-            if (scol && (unsigned)b < 6u) {
-                Ax += S * a.src[s].wx[b * 6 + si];
-                Az += S * a.src[s].wz[b * 6 + si];
-            }
-            ux = (real)2 * xc[1] - uxm + Ax;
-            uz = (real)2 * zc[1] - uzm + Az;
-        }
-        px[o] = ux;
-        pz[o] = uz;
-#pragma unroll
-        for (int q = 0; q < 3; q++) {
-            xn[q] = xc[q];
-            xc[q] = xs[q];
-            zn[q] = zc[q];
-            zc[q] = zs[q];
-        }
+        cell_update(R, X[k], X[k + 1], X[k + 2], Z[k], Z[k + 1], Z[k + 2], XM[k], ZM[k], side,
+                    j == jlast, j == 0, fx, fz, ux, uz);
+        const size_t o = (size_t)j * g.xp + i;
+        __stcs(px + o, ux);   // u^{m+1} is next read one full step later: streaming
+        __stcs(pz + o, uz);
     }
 }
 
@@ -171,14 +149,15 @@ static void launch_steps_zs(const oed_ctx *ctx, int nsolve, cudaStream_t st, cud
     a.trace = (real *)ctx->d_trace;
     a.rec = ctx->d_rec;
     a.g = g;
-    if (ev0) cudaEventRecord(ev0, st);
+    // external event records so they become event nodes of a captured graph
+    if (ev0) cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal);
     for (int m = 0; m < g.nsteps; m++) {
         a.cur = (m & 1) ? u1 : u0;
         a.nxt = (m & 1) ? u0 : u1;
         a.m = m;
         k_step<real, ZS><<<grid, block, 0, st>>>(a);
     }
-    if (ev1) cudaEventRecord(ev1, st);
+    if (ev1) cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
     const real *last = (g.nsteps & 1) ? u1 : u0;
     k_gather<real><<<nsolve, 128, 0, st>>>(last, (real *)ctx->d_trace, ctx->d_rec, g, g.nsteps,
                                            nsolve);
@@ -189,11 +168,58 @@ static void launch_steps(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEv
                          cudaEvent_t ev1)
 {
     switch (ctx->tune.zs) {
-    case 4: launch_steps_zs<real, 4>(ctx, nsolve, st, ev0, ev1); break;
-    case 16: launch_steps_zs<real, 16>(ctx, nsolve, st, ev0, ev1); break;
-    case 32: launch_steps_zs<real, 32>(ctx, nsolve, st, ev0, ev1); break;
-    default: launch_steps_zs<real, 8>(ctx, nsolve, st, ev0, ev1); break;
+    case 2: launch_steps_zs<real, 2>(ctx, nsolve, st, ev0, ev1); break;
+    case 8: launch_steps_zs<real, 8>(ctx, nsolve, st, ev0, ev1); break;
+    default: launch_steps_zs<real, 4>(ctx, nsolve, st, ev0, ev1); break;
     }
+}
+
+// Autotuner probe: nrep stencil launches for nsolve solves with the context's
+// current tuning, bracketed by ev0 / ev1 (fields and traces are scratch here).
+template <typename real, int ZS>
+static void probe_zs(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st, cudaEvent_t ev0,
+                     cudaEvent_t ev1)
+{
+    const Geometry &g = ctx->g;
+    const int wz = ctx->tune.wz;
+    dim3 block(32, wz);
+    const int rows_per_block = wz * ZS;
+    dim3 grid((g.nx + 31) / 32, (g.nz + rows_per_block - 1) / rows_per_block, nsolve);
+    StepArgs<real> a;
+    a.rows = (const RowCoef<real> *)ctx->d_rows;
+    a.src = (const SourceDesc<real> *)ctx->d_src;
+    a.stf = (const real *)ctx->d_stf;
+    a.trace = (real *)ctx->d_trace;
+    a.rec = ctx->d_rec;
+    a.g = g;
+    cudaEventRecord(ev0, st);
+    for (int m = 0; m < nrep; m++) {
+        a.cur = (real *)((m & 1) ? ctx->d_u1 : ctx->d_u0);
+        a.nxt = (real *)((m & 1) ? ctx->d_u0 : ctx->d_u1);
+        a.m = m % g.nsteps;
+        k_step<real, ZS><<<grid, block, 0, st>>>(a);
+    }
+    cudaEventRecord(ev1, st);
+}
+
+template <typename real>
+static void probe_real(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st, cudaEvent_t ev0,
+                       cudaEvent_t ev1)
+{
+    switch (ctx->tune.zs) {
+    case 2: probe_zs<real, 2>(ctx, nsolve, nrep, st, ev0, ev1); break;
+    case 8: probe_zs<real, 8>(ctx, nsolve, nrep, st, ev0, ev1); break;
+    default: probe_zs<real, 4>(ctx, nsolve, nrep, st, ev0, ev1); break;
+    }
+}
+
+void launch_step_probe(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st, cudaEvent_t ev0,
+                       cudaEvent_t ev1)
+{
+    if (ctx->precision == OED_FP64)
+        probe_real<double>(ctx, nsolve, nrep, st, ev0, ev1);
+    else
+        probe_real<float>(ctx, nsolve, nrep, st, ev0, ev1);
 }
 
 // Zero both level buffers (u^0 = u^{-1} = 0, Eq. elastic_2nd) and run all steps;
