@@ -31,8 +31,13 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "EIG evals/s & stencil Gcell-upd/s (% HBM roofline) at rel err<=1e-3; p50/p99"
-STENCIL_SRC = os.path.join(ROOT, "paper_1502_07873_gb300", "csrc", "stencil.cu")
 BYTES_PER_CELL_UPDATE = {"f32": 24, "f64": 48}   # read u^m, u^{m-1}; write u^{m+1}; 2 comps
+# FP32 operations of one interior node update (both components, Eq. Full_Disc as
+# written in stencil_cell.cuh): 21 per divergence component + 4 per leap-frog update
+FLOPS_PER_CELL_UPDATE = 50
+# FP32 peak derived from the unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 (FMA)
+# x 2.07 GHz maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -48,6 +53,11 @@ def parse():
     ap.add_argument("--cpu-sample-nodes", type=int, default=2)
     ap.add_argument("--nodes", type=int, default=0, help="override the node count (profiling runs)")
     ap.add_argument("--sigma", type=float, default=0.0, help="use this noise std instead of 1%% of peak")
+    ap.add_argument("--tuning", default="auto",
+                    help="stencil kernel: auto, or C,rows,warps (C>0 cluster-resident)")
+    ap.add_argument("--jacobian", default="pairs", choices=["pairs", "difference"])
+    ap.add_argument("--no-difference", action="store_true",
+                    help="skip the extra measurement of the difference-form Jacobian")
     return ap.parse_args()
 
 
@@ -56,11 +66,6 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
-
-
-def stencil_hash() -> str:
-    with open(STENCIL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def measured_peaks():
@@ -72,16 +77,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(workload: str, precision: str):
-    """DRAM bytes per cell-update of the stencil kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel source changed since."""
+KERNEL_SOURCES = {"k_resident": ("resident.cu", "stencil_cell.cuh", "oed_internal.cuh"),
+                  "k_step": ("stencil.cu", "stencil_cell.cuh", "oed_internal.cuh")}
+
+
+def kernel_sources_hash(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1502_07873_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per cell-update of a stencil kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel sources changed since."""
     p = os.path.join(ROOT, "profiles", "stencil_dram_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get(precision)
-    if not e or e.get("stencil_sha") != stencil_hash():
+    e = d.get(kernel)
+    if not e or e.get("sources_sha") != kernel_sources_hash(kernel):
         return None
     return float(e["dram_bytes_per_cell_update"])
 
@@ -239,7 +256,14 @@ def run_ours(args, rank, world, local):
     eig = torch.empty(1, dtype=torch.float64, device=dev)
     nbad = torch.empty(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    tuning = ctx.autotune(nsolve, stream=stream)   # launch shape of the stencil, set once
+    if args.jacobian == "difference":
+        ctx.jacobian = P.OED_JAC_DIFFERENCE
+        nsolve = 7 * w.n_nodes
+    if args.tuning == "auto":
+        tuning = ctx.autotune(nsolve, stream=stream)   # launch shape of the stencil, set once
+    else:
+        ctx.set_tuning(*[int(x) for x in args.tuning.split(",")])
+        tuning = ctx.tuning
 
     def step():
         P.oed_hessian(ctx, theta, w.prior_lo, w.prior_hi, w.rel_step, sigma, H, stream=stream)
@@ -294,6 +318,34 @@ def run_ours(args, rank, world, local):
                "h2d_bytes_per_step": int(th_h.numel() * 8 + w_h.numel() * 8),
                "d2h_bytes_per_step": 8 + 4}
 
+    # the same evaluation with the difference-form Jacobian (7 solves per node)
+    diff = None
+    if args.jacobian == "pairs" and not args.no_difference:
+        ctx.jacobian = P.OED_JAC_DIFFERENCE
+        dtun = ctx.autotune(7 * w.n_nodes, stream=stream) if args.tuning == "auto" else ctx.tuning
+        step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([dms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dms = float(t.item())
+        eig_d = float(eig.item())
+        diff = {"value": world * args.steps / (dms * 1e-3), "unit": "EIG evals/s",
+                "ms_per_step": dms / args.steps, "solves_per_gpu": 7 * w.n_nodes, "eig": eig_d,
+                "rel_diff_vs_pairs": abs(eig_d - eig_val) / abs(eig_val),
+                "stencil_kernel": ("cluster-resident, %d CTAs per solve" % dtun[0]) if dtun[0]
+                else "streaming, %d rows/thread, %d warps/block" % (dtun[1], dtun[2])}
+        ctx.jacobian = P.OED_JAC_PAIRS
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -302,10 +354,33 @@ def run_ours(args, rank, world, local):
     cells = w.cells * w.nsteps * nsolve
     per_launch_cells = w.cells * nsolve
     bpc = BYTES_PER_CELL_UPDATE[args.precision]
-    st_ms = statistics.median(stencil_ms)
-    achieved = per_launch_cells * bpc / (st_ms * 1e-3) / 1e9
+    st_ms = statistics.median(stencil_ms)          # per time step of all solves
     peak, peak_kind = measured_peaks()
-    traffic_bpc = ncu_traffic(w.name, args.precision)
+    hbm_equiv = per_launch_cells * bpc / (st_ms * 1e-3) / 1e9
+    if tuning[0] > 0:
+        # cluster-resident kernel: one launch integrates every step; the wavefield never
+        # leaves the chip, so the bound is FP32 issue, not HBM
+        launch_ms = st_ms * w.nsteps
+        flops = FLOPS_PER_CELL_UPDATE * cells
+        achieved = flops / (launch_ms * 1e-3) / 1e12
+        tb = ncu_traffic("k_resident")
+        roofline = {"bound": "alu", "kernel": "k_resident (cluster-resident leap-frog, all steps)",
+                    "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                    "algorithmic_flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
+                    "traffic": (tb * cells if tb is not None else None), "launch_ms": launch_ms,
+                    "hbm_equivalent": {"gbs": hbm_equiv, "frac_of_measured_hbm": hbm_equiv / peak,
+                                       "note": "24 B per cell-update a streaming kernel would move"}}
+        launches_per_step = 5
+    else:
+        tb = ncu_traffic("k_step")
+        roofline = {"bound": "hbm", "kernel": "k_step (streaming leap-frog, one step)",
+                    "achieved": hbm_equiv, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": hbm_equiv / peak, "algorithmic_bytes_per_cell_update": bpc,
+                    "traffic": (tb * per_launch_cells if tb is not None else None),
+                    "launch_ms": st_ms}
+        launches_per_step = w.nsteps + 5
     value = world * args.steps / (total_ms * 1e-3)
     cb = None
     if not args.no_cpu_baseline and world == 1:
@@ -323,6 +398,9 @@ def run_ours(args, rank, world, local):
         "config": {"workload": w.name, "grid": f"{w.nx}x{w.nz}", "h_m": w.h, "time_steps": w.nsteps,
                    "nodes_per_gpu": w.n_nodes, "solves_per_gpu": nsolve, "receivers": w.nrec,
                    "precision": f"{args.precision} stencil; f64 jacobian, hessian, log-det, sum",
+                   "jacobian": (f"{args.jacobian}: " + ("15 solves per node, FP64 subtraction of the "
+                                "+/- seismograms" if args.jacobian == "pairs" else
+                                "7 solves per node driven by FP64 forcing differences")),
                    "parallelism": f"replicas x{world} (independent node batches)",
                    "stencil_kernel": ("cluster-resident, %d CTAs per solve" % tuning[0]) if tuning[0]
                    else "streaming, %d rows/thread, %d warps/block" % (tuning[1], tuning[2]),
@@ -332,14 +410,11 @@ def run_ours(args, rank, world, local):
         "latency_ms": {"p50": pct(0.5), "p99": pct(0.99)},
         "eig": eig_val,
         "sigma": sigma,
-        "roofline": {"bound": "hbm", "kernel": "k_step (leap-frog stencil)", "achieved": achieved,
-                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "algorithmic_bytes_per_cell_update": bpc,
-                     "traffic": (traffic_bpc * per_launch_cells if traffic_bpc else None),
-                     "launch_ms": st_ms},
+        "roofline": roofline,
         "clocks": clk.summary(),
-        "gpu_launches": args.steps * (w.nsteps + 5),
+        "gpu_launches": args.steps * launches_per_step,
         "e2e": e2e,
+        "jacobian_difference_form": diff,
     }
     if cb:
         out["cpu_baseline"] = cb

@@ -48,6 +48,10 @@ extern "C" {
 #define OED_FP32 0 /* stencil time stepping in FP32 (Jacobian, H_1, log-det in FP64) */
 #define OED_FP64 1 /* everything in FP64 */
 
+#define OED_JAC_PAIRS 0      /* 2 N_theta + 1 solves per node: centre, theta +/- d_j e_j */
+#define OED_JAC_DIFFERENCE 1 /* N_theta solves per node, each driven by the FP64 forcing
+                                difference f(theta + d_j e_j) - f(theta - d_j e_j) */
+
 #define OED_NTHETA 7
 #define OED_NH 28 /* unique entries of a symmetric 7x7 matrix, row-major upper triangle */
 
@@ -72,8 +76,8 @@ typedef struct {
 } oed_problem;
 
 /* Create a context on the current CUDA device with device workspace for up to
- * max_solves simultaneous forward solves (oed_hessian uses 15 per node and
- * processes nodes in chunks of max_solves / 15).  Returns OED_ENOMEM if the
+ * max_solves (1..65535) simultaneous forward solves (oed_hessian uses 15 or 7
+ * per node, see oed_set_jacobian, and processes nodes in chunks).  Returns OED_ENOMEM if the
  * workspace does not fit.  *ctx is set to NULL on failure. */
 int oed_create(oed_ctx **ctx, const oed_problem *p, int max_solves);
 
@@ -119,10 +123,27 @@ int oed_get_tuning(const oed_ctx *ctx, int *cluster_size, int *rows_per_thread,
                    int *warps_per_block);
 int oed_set_tuning(oed_ctx *ctx, int cluster_size, int rows_per_thread, int warps_per_block);
 
+/* Jacobian form of oed_hessian (default OED_JAC_PAIRS).  Both give the same
+ * central difference J_j = (g(theta + d_j e_j) - g(theta - d_j e_j)) / (2 d_j):
+ *  - OED_JAC_PAIRS runs the 2 N_theta + 1 perturbed solves of each node and
+ *    subtracts the +/- seismograms in FP64;
+ *  - OED_JAC_DIFFERENCE runs N_theta solves per node, solve j driven by the
+ *    difference of the two forcings formed in FP64 (on the 7x7 union of the two
+ *    source patches, or as a difference of time functions for t_s, omega_s).
+ *    The scheme (Eq. Full_Disc) is linear in the forcing with theta-independent
+ *    coefficients, so its seismogram equals g(theta + d_j e_j) - g(theta - d_j e_j)
+ *    exactly in exact arithmetic; in FP32 it avoids the cancellation of the pairs
+ *    form and halves the solves.  Requires 2 d_j < h for j = x_s, z_s (else the
+ *    node's status is OED_EINVAL).
+ * The node chunk (oed_chunk_nodes) is max_solves / 15 or max_solves / 7. */
+int oed_set_jacobian(oed_ctx *ctx, int mode);
+int oed_get_jacobian(const oed_ctx *ctx);
+
 /* Smallest cluster size of the resident kernel for this context, 0 if none. */
 int oed_resident_min_cluster(const oed_ctx *ctx);
 
-/* Largest node chunk oed_hessian processes per pass (max_solves / 15). */
+/* Largest node chunk oed_hessian processes per pass (max_solves / 15, or / 7 in
+ * the difference form). */
 int oed_chunk_nodes(const oed_ctx *ctx);
 
 /* Forward map (Eq. forward_model): seismograms of n source vectors.

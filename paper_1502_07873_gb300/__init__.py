@@ -20,13 +20,14 @@ LIB_PATH = os.path.join(HERE, "liboed.so")
 
 OED_OK, OED_EINVAL, OED_ENOMEM, OED_ENOTPD, OED_ECUDA, OED_ETIMEOUT = range(6)
 OED_FP32, OED_FP64 = 0, 1
+OED_JAC_PAIRS, OED_JAC_DIFFERENCE = 0, 1
 NTHETA = 7
 
 SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_status_string", "oed_chunk_nodes", "oed_forward", "oed_hessian", "oed_eig",
            "oed_eig_designs", "oed_nodes_mc", "oed_nodes_smolyak", "oed_eig_host",
            "oed_last_step_time", "oed_autotune", "oed_get_tuning", "oed_set_tuning",
-           "oed_resident_min_cluster")
+           "oed_resident_min_cluster", "oed_set_jacobian", "oed_get_jacobian")
 
 
 class OedError(RuntimeError):
@@ -77,6 +78,8 @@ def library():
         "oed_get_tuning": (i, [vp, ip, ip, ip]),
         "oed_set_tuning": (i, [vp, i, i, i]),
         "oed_resident_min_cluster": (i, [vp]),
+        "oed_set_jacobian": (i, [vp, i]),
+        "oed_get_jacobian": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -204,6 +207,14 @@ class Context:
                                                       int(warps_per_block)), "oed_set_tuning")
 
     @property
+    def jacobian(self) -> int:
+        return int(library().oed_get_jacobian(self.handle))
+
+    @jacobian.setter
+    def jacobian(self, mode: int):
+        _check(self.handle, library().oed_set_jacobian(self.handle, int(mode)), "oed_set_jacobian")
+
+    @property
     def resident_min_cluster(self) -> int:
         return int(library().oed_resident_min_cluster(self.handle))
 
@@ -305,3 +316,4 @@ def oed_eig_host(ctx: Context, theta, w, lo, hi, rel_step: float, sigma: float, 
                                 ctypes.byref(bad))
     _check(ctx.handle, rc, "oed_eig_host")
     return eig.value, dkl, bad.value
+

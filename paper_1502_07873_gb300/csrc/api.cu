@@ -80,7 +80,7 @@ struct Sizes {
 static Sizes sizes(const Geometry &g, int precision, int max_solves)
 {
     const size_t e = precision == OED_FP64 ? 8 : 4;
-    const int chunk = std::max(1, max_solves / kNP);
+    const int chunk = std::max(1, max_solves / kND);   // the larger of the two node chunks
     Sizes s;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     s.u = al((size_t)max_solves * g.solve_stride * e);
@@ -172,8 +172,8 @@ int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
         fprintf(stderr, "oed_create: %s\n", why.c_str());
         return OED_EINVAL;
     }
-    if (max_solves < kNP || max_solves > 65535) {
-        fprintf(stderr, "oed_create: max_solves must be in 15..65535\n");
+    if (max_solves < 1 || max_solves > 65535) {
+        fprintf(stderr, "oed_create: max_solves must be in 1..65535\n");
         return OED_EINVAL;
     }
     oed_ctx *ctx = new (std::nothrow) oed_ctx();
@@ -362,6 +362,20 @@ int oed_set_tuning(oed_ctx *ctx, int cluster_size, int rows_per_thread, int warp
     return OED_OK;
 }
 
+int oed_set_jacobian(oed_ctx *ctx, int mode)
+{
+    if (!ctx) return OED_EINVAL;
+    if (mode != OED_JAC_PAIRS && mode != OED_JAC_DIFFERENCE)
+        return set_err(ctx, OED_EINVAL, "oed_set_jacobian: OED_JAC_PAIRS or OED_JAC_DIFFERENCE");
+    ctx->jac_mode = mode;
+    return OED_OK;
+}
+
+int oed_get_jacobian(const oed_ctx *ctx)
+{
+    return ctx ? ctx->jac_mode : -1;
+}
+
 int oed_resident_min_cluster(const oed_ctx *ctx)
 {
     return ctx ? resident_cluster_size(ctx) : 0;
@@ -369,7 +383,7 @@ int oed_resident_min_cluster(const oed_ctx *ctx)
 
 int oed_chunk_nodes(const oed_ctx *ctx)
 {
-    return ctx ? std::max(1, ctx->max_solves / kNP) : 0;
+    return ctx ? std::max(1, ctx->max_solves / solves_per_node(ctx)) : 0;
 }
 
 int oed_forward(oed_ctx *ctx, const double *theta, int n, double *g, void *stream)
@@ -399,6 +413,8 @@ int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, cons
         return set_err(ctx, OED_EINVAL, "oed_hessian: rel_step and sigma must be positive");
     if (ctx->g.nrec > kMaxRecHessian)
         return set_err(ctx, OED_EINVAL, "oed_hessian: at most 256 receivers");
+    if (ctx->max_solves < solves_per_node(ctx))
+        return set_err(ctx, OED_EINVAL, "oed_hessian: max_solves below the solves of one node");
     if (nwin < 0 || nwin > 15 || (nwin > 0 && !win_levels) || (H_rec && nwin == 0))
         return set_err(ctx, OED_EINVAL, "oed_hessian: 0..15 windows; H_rec needs windows");
     double inv2d[kNT], d[kNT];
@@ -422,8 +438,9 @@ int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, cons
     const int chunk = oed_chunk_nodes(ctx);
     for (int off = 0; off < n; off += chunk) {
         const int nb = std::min(chunk, n - off);
-        launch_sources(ctx, theta + (size_t)off * kNT, nb, kNP, d, st);
-        int rc = run_steps(ctx, nb * kNP, st);
+        const int P = solves_per_node(ctx);
+        launch_sources(ctx, theta + (size_t)off * kNT, nb, P, d, st);
+        int rc = run_steps(ctx, nb * P, st);
         if (rc) return rc;
         launch_hessian(ctx, nb, inv2d, sigma, seg_end.data(), (int)seg_end.size(), win_seg.data(),
                        nwin, H + (size_t)off * 49,

@@ -3,10 +3,12 @@
 // (Thm 2 Eq. H1; Eq. H1_numerics; Appendix C: H_1 is a sum over receivers and
 // time levels of rank-one terms, so per-receiver and per-window partial sums add up).
 //
-// Seismograms of the 15 solves of a node sit in trace[s][m][r][c] (stencil
-// precision).  The Jacobian column j is formed in FP64 from the +/- pair,
-//   J_j = (g_{+j} - g_{-j}) / (2 d_j),
-// and the 28 unique products are accumulated in FP64.  One block handles one
+// Seismograms of the solves of a node sit in trace[s][m][r][c] (stencil
+// precision).  Pairs form (15 solves per node): the Jacobian column j is formed
+// in FP64 from the +/- pair, J_j = (g_{+j} - g_{-j}) / (2 d_j).  Difference form
+// (7 solves per node): solve j already holds g_{+j} - g_{-j} (its forcing is the
+// FP64 difference of the two forcings), so J_j = g_j / (2 d_j).  The 28 unique
+// products are accumulated in FP64.  One block handles one
 // node and one time sub-segment; its threads walk the flattened (m, r, c) rows so
 // that a warp reads consecutive (r, c) of the same level (coalesced), and each
 // thread keeps a single (r, c) so its 28 partial sums belong to one receiver.
@@ -22,7 +24,7 @@ struct HArgs {
     int nsub;
 };
 
-template <typename real>
+template <typename real, bool DIFF>
 __global__ void __launch_bounds__(512) k_hsub(const real *__restrict__ trace, Geometry g,
                                               HArgs a, double *__restrict__ hsub)
 {
@@ -35,16 +37,20 @@ __global__ void __launch_bounds__(512) k_hsub(const real *__restrict__ trace, Ge
 #pragma unroll
     for (int k = 0; k < 28; k++) acc[k] = 0.0;
     const size_t per_solve = (size_t)g.nlev * nq;
-    const real *base = trace + (size_t)node * kNP * per_solve;
+    const real *base = trace + (size_t)node * (DIFF ? kND : kNP) * per_solve;
     if (mo < lanes) {
         for (int m = a.sub_m0[sub] + mo; m < a.sub_m1[sub]; m += lanes) {
             const size_t off = (size_t)m * nq + q;
             double J[kNT];
 #pragma unroll
             for (int j = 0; j < kNT; j++) {
-                const double gp = (double)base[(size_t)(1 + 2 * j) * per_solve + off];
-                const double gm = (double)base[(size_t)(2 + 2 * j) * per_solve + off];
-                J[j] = (gp - gm) * a.inv2d[j];
+                if (DIFF) {
+                    J[j] = (double)base[(size_t)j * per_solve + off] * a.inv2d[j];
+                } else {
+                    const double gp = (double)base[(size_t)(1 + 2 * j) * per_solve + off];
+                    const double gm = (double)base[(size_t)(2 + 2 * j) * per_solve + off];
+                    J[j] = (gp - gm) * a.inv2d[j];
+                }
             }
             int k = 0;
 #pragma unroll
@@ -71,7 +77,7 @@ __global__ void __launch_bounds__(512) k_hsub(const real *__restrict__ trace, Ge
 // Sum the sub-segments into per-receiver cumulative windows and the total H.
 template <typename real>
 __global__ void k_hcombine(const double *__restrict__ hsub, Geometry g, double s2, int nwin, HArgs a,
-                           const SourceDesc<real> *__restrict__ src, double *__restrict__ H,
+                           int per_node, const SourceDesc<real> *__restrict__ src, double *__restrict__ H,
                            double *__restrict__ H_rec, int *__restrict__ status)
 {
     const int node = blockIdx.x;
@@ -82,7 +88,7 @@ __global__ void k_hcombine(const double *__restrict__ hsub, Geometry g, double s
     if (threadIdx.x < 28) tot[threadIdx.x] = 0.0;
     if (threadIdx.x == 0) {
         int o = 1;
-        for (int p = 0; p < kNP; p++) o &= src[(size_t)node * kNP + p].ok;
+        for (int p = 0; p < per_node; p++) o &= src[(size_t)node * per_node + p].ok;
         ok = o;
     }
     __syncthreads();
@@ -155,17 +161,26 @@ void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double s
     const int threads = hsub_threads(g.nrec);
     const size_t smem = (size_t)threads * 29 * sizeof(double);
     dim3 grid(nnode, nsub);
-    if (ctx->precision == OED_FP64)
-        k_hsub<double><<<grid, threads, smem, st>>>((const double *)ctx->d_trace, g, a, ctx->d_hseg);
-    else
-        k_hsub<float><<<grid, threads, smem, st>>>((const float *)ctx->d_trace, g, a, ctx->d_hseg);
+    const bool diff = ctx->jac_mode == OED_JAC_DIFFERENCE;
+    if (ctx->precision == OED_FP64) {
+        if (diff)
+            k_hsub<double, true><<<grid, threads, smem, st>>>((const double *)ctx->d_trace, g, a, ctx->d_hseg);
+        else
+            k_hsub<double, false><<<grid, threads, smem, st>>>((const double *)ctx->d_trace, g, a, ctx->d_hseg);
+    } else {
+        if (diff)
+            k_hsub<float, true><<<grid, threads, smem, st>>>((const float *)ctx->d_trace, g, a, ctx->d_hseg);
+        else
+            k_hsub<float, false><<<grid, threads, smem, st>>>((const float *)ctx->d_trace, g, a, ctx->d_hseg);
+    }
     const double s2 = 1.0 / (sigma * sigma);
+    const int per_node = diff ? kND : kNP;
     if (ctx->precision == OED_FP64)
-        k_hcombine<double><<<nnode, 256, 0, st>>>(ctx->d_hseg, g, s2, nwin, a,
+        k_hcombine<double><<<nnode, 256, 0, st>>>(ctx->d_hseg, g, s2, nwin, a, per_node,
                                                   (const SourceDesc<double> *)ctx->d_src, H, H_rec,
                                                   status);
     else
-        k_hcombine<float><<<nnode, 256, 0, st>>>(ctx->d_hseg, g, s2, nwin, a,
+        k_hcombine<float><<<nnode, 256, 0, st>>>(ctx->d_hseg, g, s2, nwin, a, per_node,
                                                  (const SourceDesc<float> *)ctx->d_src, H, H_rec,
                                                  status);
 }
@@ -181,8 +196,10 @@ int hsub_threads(int nrec)
 void hessian_init(cudaStream_t)
 {
     const int smem = 512 * 29 * (int)sizeof(double);
-    cudaFuncSetAttribute(k_hsub<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_hsub<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_hsub<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_hsub<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_hsub<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_hsub<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 }  // namespace oed

@@ -16,7 +16,10 @@
 namespace oed {
 
 constexpr int kNT = 7;    // source parameters
-constexpr int kNP = 15;   // solves per node: centre and +/- d_j e_j
+constexpr int kNP = 15;   // solves per node, pairs Jacobian: centre and +/- d_j e_j
+constexpr int kND = 7;    // solves per node, difference Jacobian: one per parameter
+constexpr int kPatch = 7; // source patch edge: the 6-point delta support, widened by one
+                          // node so the difference of two shifted patches fits
 constexpr int kMaxRec = 4096;      // receivers of a forward solve
 constexpr int kMaxRecHessian = 256; // receivers of oed_hessian / oed_eig_designs
 
@@ -41,14 +44,16 @@ struct __align__(16 * sizeof(real)) RowCoef {
     real axx, azx, axzp, axzm, azzp, azzm, lx, mxp, mxm, mz, lzp, lzm, rf, cp, cs, pad;
 };
 
-// Source of one solve: corner of the 6x6 patch and the spatial force density
+// Source of one solve: corner of the 7x7 patch and the spatial force density
 // f_x, f_z (Eq. source with the regularised delta / delta' of Sec. 3.3.2),
-// already multiplied by dt^2/nu of the patch rows.
+// already multiplied by dt^2/nu of the patch rows.  The forcing at step m is
+// stf[m] * w.  For a difference solve w (or stf) is the FP64 difference of the
+// +d_j and -d_j forcings.
 template <typename real>
 struct SourceDesc {
     int i0, j0, ok, pad;
-    real wx[36];
-    real wz[36];
+    real wx[kPatch * kPatch];
+    real wz[kPatch * kPatch];
 };
 
 struct Geometry {
@@ -89,6 +94,7 @@ struct oed_ctx {
     int nseg_max = 0;
     size_t bytes = 0;
     oed::StepTuning tune{4, 4, 0};
+    int jac_mode = OED_JAC_PAIRS;   // Jacobian form of oed_hessian
     // host-path staging
     cudaStream_t own_stream = nullptr;
     double *h_stage_theta = nullptr, *h_stage_w = nullptr, *h_stage_H = nullptr,
@@ -106,9 +112,13 @@ namespace oed {
 int set_err(oed_ctx *ctx, int code, const std::string &msg);
 int cuda_err(oed_ctx *ctx, cudaError_t e, const char *what);
 
-// source.cu
+// source.cu: per_node 1 (forward), kNP (pairs Jacobian) or kND (difference Jacobian)
 void launch_sources(const oed_ctx *ctx, const double *theta_nodes, int nnode, int per_node,
                     const double *step, cudaStream_t s);
+inline int solves_per_node(const oed_ctx *ctx)
+{
+    return ctx->jac_mode == OED_JAC_DIFFERENCE ? kND : kNP;
+}
 void launch_rows(oed_ctx *ctx, cudaStream_t s);
 
 // stencil.cu

@@ -12,9 +12,14 @@
 // barrier (arrive.release / wait.acquire) per step orders the writes of step m
 // before the reads of step m+1 and the reads of step m before the overwrites of
 // step m+1.  Every thread of every CTA executes the same number of barriers.
+// Each thread owns a pair of adjacent columns (64-bit shared loads and stores)
+// and marches down a segment of the slab's rows with a 3-row x 4-column register
+// window per component; the surface row, the bottom row and the rows whose
+// neighbour lives in another CTA are peeled off the main loop, and the source
+// term is added after the sweep to the few patch nodes.
 // HBM traffic is only the seismogram samples and the source time function: the
-// wavefield never leaves the chip, so this kernel is bound by shared-memory
-// traffic and FP32 issue, not by HBM.
+// wavefield never leaves the chip, so this kernel is bound by instruction issue
+// and shared-memory traffic, not by HBM.
 #include "stencil_cell.cuh"
 
 namespace oed {
@@ -71,28 +76,65 @@ __device__ __forceinline__ float ld_cluster(unsigned addr)
     return v;
 }
 
-// three horizontal neighbours of row `l` (local index, may be -1 or nrows) of one
-// component buffer; rows outside the slab come from the neighbouring CTA
-__device__ __forceinline__ void load_row(const float *buf, int l, int nrows, int Rfull, int xp, int im,
-                                         int i, int ip, unsigned rank, float *v)
+// Row access for a thread owning the column pair (c, c+1), c even: the values at
+// columns c-1, c, c+1, c+2 of one component of a local row (v[0..3]).
+__device__ __forceinline__ void row4_local(const float *row, int c, int cm, int cp2, float *v)
+{
+    const float2 mid = *reinterpret_cast<const float2 *>(row + c);
+    v[0] = row[cm];
+    v[1] = mid.x;
+    v[2] = mid.y;
+    v[3] = row[cp2];
+}
+
+// The same for row l of the slab, where l may be -1 (last row of CTA rank-1) or
+// nrows (first row of CTA rank+1): those come from the neighbour's shared memory.
+__device__ __forceinline__ void row4_any(const float *buf, int l, int nrows, int Rfull, int xp, int c,
+                                         int cm, int cp2, unsigned rank, float *v)
 {
     if (l >= 0 && l < nrows) {
-        const float *p = buf + l * xp;
-        v[0] = p[im];
-        v[1] = p[i];
-        v[2] = p[ip];
+        row4_local(buf + l * xp, c, cm, cp2, v);
     } else {
-        // l == -1: last row of CTA rank-1 (always a full slab); l == nrows: first row of rank+1
         const int lr = (l < 0) ? Rfull - 1 : 0;
         const unsigned nb = (l < 0) ? rank - 1 : rank + 1;
         const unsigned base = remote_addr(smem_addr(buf + lr * xp), nb);
-        v[0] = ld_cluster(base + 4u * im);
-        v[1] = ld_cluster(base + 4u * i);
-        v[2] = ld_cluster(base + 4u * ip);
+        v[0] = ld_cluster(base + 4u * cm);
+        v[1] = ld_cluster(base + 4u * c);
+        v[2] = ld_cluster(base + 4u * (c + 1));
+        v[3] = ld_cluster(base + 4u * cp2);
     }
 }
 
-__global__ void __launch_bounds__(1024, 1) k_resident(ResArgs a)
+// Update of the two nodes (c, c+1) of one row from 3x4 windows of u_x and u_z
+// (node c uses window columns 0..2, node c+1 columns 1..3).  ux, uz hold u^{m-1}
+// on entry and u^{m+1} on exit.  TOP / BOTTOM select the surface closure and the
+// absorbing bottom row.
+template <bool TOP, bool BOTTOM>
+__device__ __forceinline__ void pair_update(const RowCoef<float> &R, const float *xn, const float *xc,
+                                            const float *xs, const float *zn, const float *zc,
+                                            const float *zs, float2 &ux, float2 &uz, int sideA,
+                                            int sideB)
+{
+    float a, b;
+    cell_update(R, xn, xc, xs, zn, zc, zs, ux.x, uz.x, sideA, BOTTOM, TOP, 0.0f, 0.0f, a, b);
+    ux.x = a;
+    uz.x = b;
+    cell_update(R, xn + 1, xc + 1, xs + 1, zn + 1, zc + 1, zs + 1, ux.y, uz.y, sideB, BOTTOM, TOP, 0.0f,
+                0.0f, a, b);
+    ux.y = a;
+    uz.y = b;
+}
+
+#define OED_ROTATE()                                                                               \
+    _Pragma("unroll") for (int q = 0; q < 4; q++)                                                  \
+    {                                                                                              \
+        xn[q] = xc[q];                                                                             \
+        xc[q] = xs[q];                                                                             \
+        zn[q] = zc[q];                                                                             \
+        zc[q] = zs[q];                                                                             \
+    }
+
+__global__ void __launch_bounds__(768, 1) k_resident(ResArgs a)
 {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
@@ -110,62 +152,105 @@ __global__ void __launch_bounds__(1024, 1) k_resident(ResArgs a)
     for (int k = tid; k < 4 * R * xp; k += nthr) sm[k] = 0.0f;   // u^0 = u^{-1} = 0
     for (int k = tid; k < nrows; k += nthr) coef[k] = a.rows[j0 + k];
 
-    const int i = threadIdx.x + 32 * (threadIdx.y % ((g.nx + 31) / 32));
-    const int seg = threadIdx.y / ((g.nx + 31) / 32);
-    const bool active = i < g.nx && seg < a.nseg;
-    const int im = i > 0 ? i - 1 : 0;
-    const int ip = i < g.nx - 1 ? i + 1 : g.nx - 1;
-    const int side = (i == 0) ? 1 : ((i == g.nx - 1) ? 2 : 0);
+    // thread -> column pair (c, c+1) and row segment [l0, l1) of the slab
+    const int ncolw = (g.nx + 63) / 64;
+    const int c = 2 * (threadIdx.x + 32 * (threadIdx.y % ncolw));
+    const int seg = threadIdx.y / ncolw;
+    const bool active = c < g.nx && seg < a.nseg;
+    const int cm = c > 0 ? c - 1 : 0;
+    const int cp2 = c + 2 < g.nx ? c + 2 : g.nx - 1;
+    const int sideA = (c == 0) ? 1 : ((c == g.nx - 1) ? 2 : 0);
+    const int sideB = (c + 1 == g.nx - 1) ? 2 : 0;
+    const bool validB = c + 1 < g.nx;
     const int l0 = seg * a.rps;
     const int l1 = min(l0 + a.rps, nrows);
+    const bool top = (j0 + l0 == 0);
     const SourceDesc<float> *sd = a.src + s;
-    const int si = i - sd->i0;
     const int sj = sd->j0;
-    const bool scol = (unsigned)si < 6u;
+    const int siA = c - sd->i0, siB = c + 1 - sd->i0;
+    const bool scolA = (unsigned)siA < (unsigned)kPatch;
+    const bool scolB = validB && (unsigned)siB < (unsigned)kPatch;
     const float *stf = a.stf + (size_t)s * g.nsteps;
     float *trace = a.trace + (size_t)s * g.nlev * g.nrec * 2;
     cluster_barrier();
 
     for (int m = 0; m < g.nsteps; m++) {
         const float *cx = (m & 1) ? Bx : Ax, *cz = (m & 1) ? Bz : Az;
-        float *nx_ = (m & 1) ? Ax : Bx, *nz_ = (m & 1) ? Az : Bz;
+        float *nxb = (m & 1) ? Ax : Bx, *nzb = (m & 1) ? Az : Bz;
         if (rank == 0)
             for (int q = tid; q < 2 * g.nrec; q += nthr)
                 trace[(size_t)m * g.nrec * 2 + q] = (q & 1 ? cz : cx)[a.rec[q >> 1]];
         if (active && l0 < l1) {
-            const float S = scol ? stf[m] : 0.0f;
-            float xn[3], xc[3], xs[3], zn[3], zc[3], zs[3];
-            // j - 1 of the first row: for the surface row (j = 0) it is never used
-            const int ln = (j0 + l0 == 0) ? l0 : l0 - 1;
-            load_row(cx, ln, nrows, R, xp, im, i, ip, rank, xn);
-            load_row(cz, ln, nrows, R, xp, im, i, ip, rank, zn);
-            load_row(cx, l0, nrows, R, xp, im, i, ip, rank, xc);
-            load_row(cz, l0, nrows, R, xp, im, i, ip, rank, zc);
-            for (int l = l0; l < l1; l++) {
-                const int j = j0 + l;
-                // j + 1 of the bottom row is never used
-                const int ls = (j == g.nz - 1) ? l : l + 1;
-                load_row(cx, ls, nrows, R, xp, im, i, ip, rank, xs);
-                load_row(cz, ls, nrows, R, xp, im, i, ip, rank, zs);
-                const int o = l * xp + i;
-                const int b = j - sj;
-                float fx = 0.0f, fz = 0.0f;
-                if (scol && (unsigned)b < 6u) {
-                    fx = S * sd->wx[b * 6 + si];
-                    fz = S * sd->wz[b * 6 + si];
+            float xn[4], xc[4], xs[4], zn[4], zc[4], zs[4];
+            // row above the first node (not used on the surface row)
+            const int ln = top ? l0 : l0 - 1;
+            row4_any(cx, ln, nrows, R, xp, c, cm, cp2, rank, xn);
+            row4_any(cz, ln, nrows, R, xp, c, cm, cp2, rank, zn);
+            row4_local(cx + l0 * xp, c, cm, cp2, xc);
+            row4_local(cz + l0 * xp, c, cm, cp2, zc);
+            int l = l0;
+            if (top) {   // surface row
+                row4_any(cx, l + 1, nrows, R, xp, c, cm, cp2, rank, xs);
+                row4_any(cz, l + 1, nrows, R, xp, c, cm, cp2, rank, zs);
+                const RowCoef<float> Rc = coef[l];
+                float2 *px = reinterpret_cast<float2 *>(nxb + l * xp + c);
+                float2 *pz = reinterpret_cast<float2 *>(nzb + l * xp + c);
+                float2 ux = *px, uz = *pz;
+                pair_update<true, false>(Rc, xn, xc, xs, zn, zc, zs, ux, uz, sideA, sideB);
+                *px = ux;
+                *pz = uz;
+                OED_ROTATE();
+                l++;
+            }
+            // rows whose lower neighbour is a local row and that are not the bottom row
+            const int lstop = min(l1, nrows - 1);
+#pragma unroll 2
+            for (; l < lstop; l++) {
+                row4_local(cx + (l + 1) * xp, c, cm, cp2, xs);
+                row4_local(cz + (l + 1) * xp, c, cm, cp2, zs);
+                const RowCoef<float> Rc = coef[l];
+                float2 *px = reinterpret_cast<float2 *>(nxb + l * xp + c);
+                float2 *pz = reinterpret_cast<float2 *>(nzb + l * xp + c);
+                float2 ux = *px, uz = *pz;
+                pair_update<false, false>(Rc, xn, xc, xs, zn, zc, zs, ux, uz, sideA, sideB);
+                *px = ux;
+                *pz = uz;
+                OED_ROTATE();
+            }
+            // what is left: a last interior row whose lower neighbour sits in CTA rank+1,
+            // or the absorbing bottom row
+            for (; l < l1; l++) {
+                const RowCoef<float> Rc = coef[l];
+                float2 *px = reinterpret_cast<float2 *>(nxb + l * xp + c);
+                float2 *pz = reinterpret_cast<float2 *>(nzb + l * xp + c);
+                float2 ux = *px, uz = *pz;
+                if (j0 + l == g.nz - 1) {
+                    pair_update<false, true>(Rc, xn, xc, xc, zn, zc, zc, ux, uz, sideA, sideB);
+                } else {
+                    row4_any(cx, l + 1, nrows, R, xp, c, cm, cp2, rank, xs);
+                    row4_any(cz, l + 1, nrows, R, xp, c, cm, cp2, rank, zs);
+                    pair_update<false, false>(Rc, xn, xc, xs, zn, zc, zs, ux, uz, sideA, sideB);
                 }
-                const RowCoef<float> Rc = coef[l];   // four 16-byte broadcast loads
-                float ux, uz;
-                cell_update(Rc, xn, xc, xs, zn, zc, zs, nx_[o], nz_[o], side, j == g.nz - 1, j == 0,
-                            fx, fz, ux, uz);
-                nx_[o] = ux;
-                nz_[o] = uz;
-#pragma unroll
-                for (int q = 0; q < 3; q++) {
-                    xn[q] = xc[q];
-                    xc[q] = xs[q];
-                    zn[q] = zc[q];
-                    zc[q] = zs[q];
+                *px = ux;
+                *pz = uz;
+                OED_ROTATE();
+            }
+            // source term: u^{m+1} += dt^2/nu f^m on the patch nodes this thread owns,
+            // added last as in the node update of the streaming kernel
+            if (scolA || scolB) {
+                const float S = stf[m];
+                for (int bb = 0; bb < kPatch; bb++) {
+                    const int lj = sj + bb - j0;
+                    if (lj < l0 || lj >= l1) continue;
+                    const int o = lj * xp + c;
+                    if (scolA) {
+                        nxb[o] += S * sd->wx[bb * kPatch + siA];
+                        nzb[o] += S * sd->wz[bb * kPatch + siA];
+                    }
+                    if (scolB) {
+                        nxb[o + 1] += S * sd->wx[bb * kPatch + siB];
+                        nzb[o + 1] += S * sd->wz[bb * kPatch + siB];
+                    }
                 }
             }
         }
@@ -188,13 +273,13 @@ struct ResShape {
 static ResShape resident_shape(const Geometry &g, int C)
 {
     ResShape r{};
-    const int ncolw = (g.nx + 31) / 32;
-    if (ncolw > 32 || C < 1 || C > 8) return r;
+    const int ncolw = (g.nx + 63) / 64;   // warps of 32 column pairs
+    if (ncolw > 24 || C < 1 || C > 8) return r;
     const int R = (g.nz + C - 1) / C;
     if ((C - 1) * R >= g.nz) return r;   // a CTA would own no rows
     const size_t smem = (size_t)4 * R * g.xp * sizeof(float) + (size_t)R * sizeof(RowCoef<float>);
     if (smem > 227 * 1024) return r;
-    int nseg = 32 / ncolw;
+    int nseg = 24 / ncolw;   // at most 768 threads: 85 registers per thread
     if (nseg < 1) nseg = 1;
     if (nseg > R) nseg = R;
     r.C = C;

@@ -39,8 +39,42 @@ struct FdStep {
     double d[kNT];
 };
 
-// One thread block per solve.  Thread 0..35 fill the 6x6 patch; all threads
-// sample the source time function.
+// Spatial part of M grad(delta) for one parameter vector on its 6x6 support:
+// corner (kx - 2, kz - 2); f[b][a] at node (kx - 2 + a, kz - 2 + b).
+//   f_x = m_xx delta'(x) delta(z) + m_xz delta(x) delta'(z)
+//   f_z = m_xz delta'(x) delta(z) + m_zz delta(x) delta'(z)
+// Returns false if x_s / h or z_s / h is not a usable number.
+__device__ bool source_patch6(const double *th, double h, int *kx, int *kz, double *fx, double *fz)
+{
+    const double qx = th[0] / h, qz = th[1] / h;
+    const double flx = floor(qx), flz = floor(qz);
+    if (!(isfinite(qx) && isfinite(qz) && fabs(flx) < 1e9 && fabs(flz) < 1e9)) return false;
+    double dx[6], dpx[6], dz[6], dpz[6];
+    delta_weights(qx - flx, h, dx, dpx);
+    delta_weights(qz - flz, h, dz, dpz);
+    *kx = (int)flx;
+    *kz = (int)flz;
+    for (int b = 0; b < 6; b++)
+        for (int a = 0; a < 6; a++) {
+            fx[b * 6 + a] = th[4] * dpx[a] * dz[b] + th[5] * dx[a] * dpz[b];
+            fz[b * 6 + a] = th[5] * dpx[a] * dz[b] + th[6] * dx[a] * dpz[b];
+        }
+    return true;
+}
+
+__device__ __forceinline__ double stf_value(double t, double ts, double ws)
+{
+    const double u = t - ts;
+    return ws * 0.3989422804014327 * exp(-0.5 * ws * ws * u * u);   // w / sqrt(2 pi) e^{...}
+}
+
+// One thread block per solve.  per_node = 1: the node itself (forward map);
+// per_node = 15: centre and theta +/- d_j e_j (pairs Jacobian); per_node = 7:
+// solve j carries the FP64 difference of the theta + d_j e_j and theta - d_j e_j
+// forcings (difference Jacobian; by linearity of the scheme in the forcing its
+// seismogram is exactly g(theta + d_j e_j) - g(theta - d_j e_j)).  For j = x_s, z_s
+// and the moments the spatial patch differs (the two 6x6 patches are subtracted
+// on their 7x7 union); for j = t_s, omega_s the time function differs.
 template <typename real>
 __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, int per_node,
                           FdStep step, Geometry g, const RowCoef<real> *__restrict__ rows,
@@ -50,36 +84,59 @@ __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, in
     const int s = blockIdx.x;
     if (s >= nsolve) return;
     const int node = s / per_node, p = s % per_node;
-    __shared__ double th[kNT];
-    __shared__ double wts[4][6];   // dx, dpx, dz, dpz
+    const bool diff = per_node == kND;
+    __shared__ double th[kNT], tp[kNT], tm[kNT];
+    __shared__ double w7x[kPatch * kPatch], w7z[kPatch * kPatch];
     __shared__ int corner[3];
+    __shared__ int time_diff;
     if (threadIdx.x < kNT) {
-        double v = theta_nodes[(size_t)node * kNT + threadIdx.x];
-        // p = 0 centre, p = 1 + 2j: +d_j, p = 2 + 2j: -d_j
-        if (p > 0) {
-            int j = (p - 1) >> 1;
-            if ((int)threadIdx.x == j) v += ((p - 1) & 1) ? -step.d[j] : step.d[j];
-        }
-        th[threadIdx.x] = v;
-        theta_out[(size_t)s * kNT + threadIdx.x] = v;
+        const int j = threadIdx.x;
+        const double v = theta_nodes[(size_t)node * kNT + j];
+        double vs = v;
+        if (!diff && p > 0 && j == (p - 1) / 2) vs += ((p - 1) & 1) ? -step.d[j] : step.d[j];
+        th[j] = vs;
+        tp[j] = v + ((diff && j == p) ? step.d[j] : 0.0);
+        tm[j] = v - ((diff && j == p) ? step.d[j] : 0.0);
+        theta_out[(size_t)s * kNT + j] = vs;
     }
+    for (int k = threadIdx.x; k < kPatch * kPatch; k += blockDim.x) w7x[k] = w7z[k] = 0.0;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double qx = th[0] / g.h, qz = th[1] / g.h;
-        const double fx = floor(qx), fz = floor(qz);
-        int ok = isfinite(qx) && isfinite(qz) && fx > -1e9 && fx < 1e9 && fz > -1e9 && fz < 1e9;
-        int kx = ok ? (int)fx : 0, kz = ok ? (int)fz : 0;
-        double dx[6], dpx[6], dz[6], dpz[6];
-        delta_weights(qx - fx, g.h, dx, dpx);
-        delta_weights(qz - fz, g.h, dz, dpz);
-        for (int a = 0; a < 6; a++) {
-            wts[0][a] = dx[a];
-            wts[1][a] = dpx[a];
-            wts[2][a] = dz[a];
-            wts[3][a] = dpz[a];
+        double fx[36], fz[36];
+        int kx = 0, kz = 0, ok;
+        int i0, j0, span;   // span: 6 or 7 nodes of the patch actually used
+        time_diff = diff && (p == 2 || p == 3);
+        if (!diff || time_diff) {
+            ok = source_patch6(th, g.h, &kx, &kz, fx, fz);
+            i0 = kx - 2;
+            j0 = kz - 2;
+            span = 6;
+            for (int b = 0; b < 6; b++)
+                for (int a = 0; a < 6; a++) {
+                    w7x[b * kPatch + a] = fx[b * 6 + a];
+                    w7z[b * kPatch + a] = fz[b * 6 + a];
+                }
+        } else {
+            double gx[36], gz[36];
+            int kx2 = 0, kz2 = 0;
+            ok = source_patch6(tp, g.h, &kx, &kz, fx, fz) && source_patch6(tm, g.h, &kx2, &kz2, gx, gz);
+            const int kxm = min(kx, kx2), kzm = min(kz, kz2);
+            ok = ok && max(kx, kx2) - kxm <= 1 && max(kz, kz2) - kzm <= 1;
+            i0 = kxm - 2;
+            j0 = kzm - 2;
+            span = (kx != kx2 || kz != kz2) ? 7 : 6;
+            if (ok) {
+                const int ox = kx - kxm, oz = kz - kzm, ox2 = kx2 - kxm, oz2 = kz2 - kzm;
+                for (int b = 0; b < 6; b++)
+                    for (int a = 0; a < 6; a++) {
+                        w7x[(b + oz) * kPatch + a + ox] += fx[b * 6 + a];
+                        w7z[(b + oz) * kPatch + a + ox] += fz[b * 6 + a];
+                        w7x[(b + oz2) * kPatch + a + ox2] -= gx[b * 6 + a];
+                        w7z[(b + oz2) * kPatch + a + ox2] -= gz[b * 6 + a];
+                    }
+            }
         }
-        const int i0 = kx - 2, j0 = kz - 2;
-        ok = ok && i0 >= 1 && i0 + 5 <= g.nx - 2 && j0 >= 0 && j0 + 5 <= g.nz - 2;
+        ok = ok && i0 >= 1 && i0 + span - 1 <= g.nx - 2 && j0 >= 0 && j0 + span - 1 <= g.nz - 2;
         corner[0] = ok ? i0 : -100;
         corner[1] = ok ? j0 : -100;
         corner[2] = ok;
@@ -88,25 +145,17 @@ __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, in
         src[s].ok = ok;
     }
     __syncthreads();
-    if (threadIdx.x < 36) {
-        const int a = threadIdx.x % 6, b = threadIdx.x / 6;
-        const double mxx = th[4], mxz = th[5], mzz = th[6];
-        // f_x = m_xx delta'(x) delta(z) + m_xz delta(x) delta'(z)
-        // f_z = m_xz delta'(x) delta(z) + m_zz delta(x) delta'(z)
-        const double fx = mxx * wts[1][a] * wts[2][b] + mxz * wts[0][a] * wts[3][b];
-        const double fz = mxz * wts[1][a] * wts[2][b] + mzz * wts[0][a] * wts[3][b];
+    for (int k = threadIdx.x; k < kPatch * kPatch; k += blockDim.x) {
+        const int b = k / kPatch;
         const int j = corner[1] + b;
-        const double rf = corner[2] ? (double)rows[j].rf : 0.0;
-        src[s].wx[threadIdx.x] = (real)(fx * rf);
-        src[s].wz[threadIdx.x] = (real)(fz * rf);
+        const double rf = (corner[2] && j <= g.nz - 1) ? (double)rows[j].rf : 0.0;
+        src[s].wx[k] = (real)(w7x[k] * rf);
+        src[s].wz[k] = (real)(w7z[k] * rf);
     }
-    const double ts = th[2], ws = th[3];
-    const double c = ws * 0.3989422804014327;   // w / sqrt(2 pi)
-    const double nan = __longlong_as_double(0x7ff8000000000000ULL);
     for (int m = threadIdx.x; m < g.nsteps; m += blockDim.x) {
-        const double t = m * g.dt - ts;
-        double v = c * exp(-0.5 * ws * ws * t * t);
-        if (!corner[2]) v = nan;   // invalid source: poison the solve
+        const double t = m * g.dt;
+        const double v = time_diff ? stf_value(t, tp[2], tp[3]) - stf_value(t, tm[2], tm[3])
+                                   : stf_value(t, th[2], th[3]);
         stf[(size_t)s * g.nsteps + m] = (real)v;
     }
 }

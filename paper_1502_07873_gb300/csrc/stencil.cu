@@ -6,7 +6,7 @@
 //   absorbing nodes (sides, bottom; first-order Clayton-Engquist, forward in time,
 //   upwind in space):            u^{m+1} = u^m + c dt/h (u_inward^m - u^m)
 // with A_h the second-order operator built from D+, D-, D0 and a summation-by-parts
-// closure on the free surface, and f^m = S(t_m) M grad(delta) on the 6x6 source patch.
+// closure on the free surface, and f^m = S(t_m) M grad(delta) on the 7x7 source patch.
 //
 // Memory layout: u[solve][component][z][xp] with xp a multiple of 32, so every warp
 // reads and writes whole 128-byte lines.  u^{m+1} overwrites u^{m-1} in place (each
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_step(StepArgs<real> a)
     }
     const int si = i - a.src[s].i0;
     const int sj = a.src[s].j0;
-    const bool scol = (unsigned)si < 6u;
+    const bool scol = (unsigned)si < (unsigned)kPatch;
     const real S = scol ? a.stf[(size_t)s * g.nsteps + a.m] : (real)0;
 
 #pragma unroll
@@ -105,9 +105,9 @@ __global__ void __launch_bounds__(256) k_step(StepArgs<real> a)
         const RowCoef<real> R = a.rows[j];
         const int b = j - sj;
         real fx = (real)0, fz = (real)0;
-        if (scol && (unsigned)b < 6u) {
-            fx = S * a.src[s].wx[b * 6 + si];
-            fz = S * a.src[s].wz[b * 6 + si];
+        if (scol && (unsigned)b < (unsigned)kPatch) {
+            fx = S * a.src[s].wx[b * kPatch + si];
+            fz = S * a.src[s].wz[b * kPatch + si];
         }
         real ux, uz;
         cell_update(R, X[k], X[k + 1], X[k + 2], Z[k], Z[k + 1], Z[k + 2], XM[k], ZM[k], side,

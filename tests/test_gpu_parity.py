@@ -188,9 +188,10 @@ def test_resident_matches_oracle_and_streaming(P, oracle, grid, clusters):
             out = g[k].cpu().numpy()
             assert _normwise(out, ref[k]) <= 1e-4, (C, k, _normwise(out, ref[k]))
             assert _normwise(out, g_stream[k].cpu().numpy()) <= 1e-5
+    # the gain through the resident path; the layered grid's FP32 pairs Jacobian loses too
+    # many digits to cancellation, so there the difference form is used
     if grid != "homog_75x37":
-        return   # the layered grid's FP32 gain needs the difference-form Jacobian (tested below)
-    # the gain through the resident path
+        ctx.jacobian = P.OED_JAC_DIFFERENCE
     H = torch.empty((4, 7, 7), dtype=torch.float64, device=DEV)
     ctx.set_tuning(clusters[-1], 4, 4)
     sigma = 0.05
@@ -204,6 +205,37 @@ def test_resident_matches_oracle_and_streaming(P, oracle, grid, clusters):
         ld, _, ok = oracle.scaled_logdet(Href)
         d_ref = oracle.dkl(ld, 7, lp)
         assert abs(float(dkl[k].item()) - d_ref) <= 1e-3 * abs(d_ref)
+
+
+@pytest.mark.parametrize("prec,tol_h,tol_d", [(1, 1e-9, 1e-10), (0, None, 1e-4)])
+def test_difference_jacobian_matches_oracle(P, oracle, prec, tol_h, tol_d):
+    """The difference-form Jacobian (one solve per parameter driven by the FP64 forcing
+    difference) against the oracle's literal +/- pairs.  Node 0 sits exactly on a grid
+    node in x and z, so x_s - d and x_s + d fall in different cells (7-wide patch)."""
+    w = W.tiny(**GRIDS["layered_70x41"])
+    th = _thetas(w, 3, seed=21)
+    th[0, 0] = 40 * w.h
+    th[0, 1] = 18 * w.h
+    G = oracle.Grid.from_workload(w)
+    sigma = 0.05
+    ctx = P.Context(P.problem_from_workload(w, prec), max_solves=14)   # chunks of 2 nodes
+    ctx.jacobian = P.OED_JAC_DIFFERENCE
+    assert ctx.chunk_nodes == 2
+    H = torch.empty((3, 7, 7), dtype=torch.float64, device=DEV)
+    st = torch.empty(3, dtype=torch.int32, device=DEV)
+    P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, sigma, H, status=st)
+    dkl = torch.empty(3, dtype=torch.float64, device=DEV)
+    eig = torch.empty(1, dtype=torch.float64, device=DEV)
+    P.oed_eig(ctx, H, _t(np.full(3, 1 / 3)), w.prior_lo, w.prior_hi, eig, dkl=dkl)
+    assert st.cpu().tolist() == [0, 0, 0]
+    lp = oracle.log_uniform_density(w.prior_lo, w.prior_hi)
+    for k in range(3):
+        Href, _ = oracle.node_hessian(G, th[k], w.prior_lo, w.prior_hi, w.rel_step, sigma)
+        if tol_h:
+            assert _scaled(H[k].cpu().numpy(), Href) <= tol_h
+        ld, _, ok = oracle.scaled_logdet(Href)
+        d_ref = oracle.dkl(ld, 7, lp)
+        assert abs(float(dkl[k].item()) - d_ref) <= tol_d * abs(d_ref), (k, float(dkl[k].item()), d_ref)
 
 
 def test_resident_rejects_grids_that_do_not_fit(P):
