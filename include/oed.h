@@ -224,6 +224,36 @@ int oed_eig_host(oed_ctx *ctx, const double *theta, const double *w, int n, cons
                  const double *hi, double rel_step, double sigma, double *eig, double *dkl,
                  int *n_bad);
 
+/* Allocation-free Gauss-Newton Hessian from seismograms the caller already has.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory while they run, e.g. code that records work into a
+ * CUDA graph or a stream-ordered pipeline where cudaMalloc would synchronise the
+ * device or is not permitted, or an embedding application that fixes its device
+ * memory budget up front.  It computes the same H_1 as oed_hessian from given
+ * seismograms, with no context, and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   g        device [n][per_node][nlev][nrec][2] FP64, time-major seismograms of the
+ *            node's solves: per_node = 15 for the pairs form (solve 0 the centre,
+ *            1 + 2j at theta + d_j e_j, 2 + 2j at theta - d_j e_j) or 7 for the
+ *            difference form (solve j = g(theta + d_j e_j) - g(theta - d_j e_j))
+ *   lo, hi   host [7] prior box; d_j = rel_step (hi_j - lo_j); sigma the noise std
+ *   H        device [n][7][7]
+ * Its scratch is one fixed device array of OED_NOALLOC_SCRATCH_DOUBLES doubles
+ * (4 MiB) in the library, held by every GPU that loads the library until the
+ * process exits; a call needs n * min(8, nlev) * nrec * 28 of them (n * nrec <= 2340
+ * when nlev >= 8) and returns OED_ENOMEM, without launching anything, above that.
+ * Every call on a device shares that array: calls that can overlap on the GPU
+ * (different streams, or host threads) race and must be serialised by the caller.
+ * Each call writes every scratch entry it reads, so no clearing is needed.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream capture.
+ * Returns OED_OK, OED_EINVAL (bad sizes or pointers), OED_ENOMEM or OED_ECUDA. */
+#define OED_NOALLOC_SCRATCH_DOUBLES (1 << 19)
+int oed_gauss_newton_noalloc(const double *g, int n, int per_node, int nlev, int nrec,
+                             const double *lo, const double *hi, double rel_step, double sigma,
+                             double *H, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

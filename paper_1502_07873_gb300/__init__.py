@@ -27,7 +27,8 @@ SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_status_string", "oed_chunk_nodes", "oed_forward", "oed_hessian", "oed_eig",
            "oed_eig_designs", "oed_nodes_mc", "oed_nodes_smolyak", "oed_eig_host",
            "oed_last_step_time", "oed_autotune", "oed_get_tuning", "oed_set_tuning",
-           "oed_resident_min_cluster", "oed_set_jacobian", "oed_get_jacobian")
+           "oed_resident_min_cluster", "oed_set_jacobian", "oed_get_jacobian",
+           "oed_gauss_newton_noalloc")
 
 
 class OedError(RuntimeError):
@@ -80,6 +81,7 @@ def library():
         "oed_resident_min_cluster": (i, [vp]),
         "oed_set_jacobian": (i, [vp, i]),
         "oed_get_jacobian": (i, [vp]),
+        "oed_gauss_newton_noalloc": (i, [vp, i, i, i, i, dp, dp, d, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -317,3 +319,13 @@ def oed_eig_host(ctx: Context, theta, w, lo, hi, rel_step: float, sigma: float, 
     _check(ctx.handle, rc, "oed_eig_host")
     return eig.value, dkl, bad.value
 
+
+def oed_gauss_newton_noalloc(g, lo, hi, rel_step: float, sigma: float, H, stream=None):
+    """Allocation-free H_1[n][7][7] from seismograms g[n][15 or 7][nlev][nrec][2] (FP64,
+    device).  For callers that cannot allocate device memory while they run; its scratch
+    is a fixed 4 MiB array inside the library, shared by all calls on a device (calls that
+    overlap on the GPU race).  Returns the status code (0 = OED_OK)."""
+    n, per_node, nlev, nrec = g.shape[0], g.shape[1], g.shape[2], g.shape[3]
+    return int(library().oed_gauss_newton_noalloc(_ptr(g), n, per_node, nlev, nrec, _darr(lo),
+                                                  _darr(hi), float(rel_step), float(sigma), _ptr(H),
+                                                  _stream(stream)))
