@@ -43,7 +43,9 @@ extern "C" {
 #define OED_ENOMEM 2   /* device allocation failed, or a request exceeds the workspace */
 #define OED_ENOTPD 3   /* some H_1 is not positive definite (see the per-node status) */
 #define OED_ECUDA 4    /* a CUDA runtime call failed */
-#define OED_ETIMEOUT 5 /* a bounded device wait gave up */
+#define OED_ETIMEOUT 5 /* a bounded wait gave up */
+#define OED_PENDING 6  /* (serving) the request has not finished yet */
+#define OED_ECANCELED 7 /* (serving) the request was cancelled before it ran */
 
 #define OED_FP32 0 /* stencil time stepping in FP32 (Jacobian, H_1, log-det in FP64) */
 #define OED_FP64 1 /* everything in FP64 */
@@ -85,7 +87,10 @@ int oed_create(oed_ctx **ctx, const oed_problem *p, int max_solves);
  * (used for admission by HBM footprint).  Returns 0 for an invalid problem. */
 size_t oed_workspace_bytes(const oed_problem *p, int max_solves);
 
-/* Release the context and its workspace.  NULL is accepted. */
+/* Release the context and its workspace.  NULL is accepted.  The streams used
+ * with the context must be synchronised first.  The workspace is allocated and
+ * released stream-ordered (cudaMallocAsync / cudaFreeAsync on the context's own
+ * stream), so creating and destroying contexts does not stall other streams. */
 int oed_destroy(oed_ctx *ctx);
 
 /* Message of the last failing call on ctx (never NULL). */
@@ -223,6 +228,60 @@ int oed_nodes_smolyak(int dim, int level, const double *lo, const double *hi, in
 int oed_eig_host(oed_ctx *ctx, const double *theta, const double *w, int n, const double *lo,
                  const double *hi, double rel_step, double sigma, double *eig, double *dkl,
                  int *n_bad);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop for EIG queries with continuous batching.
+ *
+ * Requests (a problem, its quadrature nodes and weights, the prior box, the FD
+ * step, the noise level and the Jacobian form) are queued in arrival order.  Up
+ * to max_active requests run at once, each on its own worker thread and CUDA
+ * stream through oed_create / oed_hessian / oed_eig, so a request admitted while
+ * others are on the GPU overlaps with them on the device.  The head of the queue
+ * is admitted as soon as its device footprint (oed_server_request_bytes: context
+ * workspace for chunks of chunk_nodes nodes, plus its node, weight and Hessian
+ * arrays) fits in the part of hbm_budget_bytes not held by running requests;
+ * admission is strictly first-come first-served.  Launch shapes are autotuned on
+ * the first request of each grid shape and reused (unless
+ * OED_SERVER_NO_AUTOTUNE).  The server uses the CUDA device current at creation.
+ * ------------------------------------------------------------------------ */
+typedef struct oed_server oed_server;
+
+#define OED_SERVER_NO_AUTOTUNE 1
+
+typedef struct {
+    oed_problem problem;   /* host arrays, copied at submission */
+    int n;                 /* quadrature nodes, >= 1 */
+    const double *theta;   /* host [n][7] */
+    const double *w;       /* host [n] weights */
+    const double *lo, *hi; /* host [7] prior box */
+    double rel_step;       /* FD step as a fraction of the prior width */
+    double sigma;          /* noise standard deviation (C_eps = sigma^2 I) */
+    int jacobian;          /* OED_JAC_PAIRS or OED_JAC_DIFFERENCE */
+} oed_request;
+
+typedef struct {
+    int status;            /* OED_OK, OED_PENDING, OED_ECANCELED or the failing call's code */
+    double eig;            /* expected information gain (valid when status == OED_OK) */
+    int n_bad;             /* nodes rejected as not positive definite */
+    double t_submit, t_admit, t_done; /* seconds on the server's monotonic clock */
+    size_t footprint_bytes;           /* device memory reserved while it ran */
+} oed_result;
+
+int oed_server_create(oed_server **srv, size_t hbm_budget_bytes, int max_active, int chunk_nodes,
+                      int flags);
+/* Device bytes a request reserves while it runs (0 if the request is invalid). */
+size_t oed_server_request_bytes(const oed_request *req, int chunk_nodes);
+/* Queue a request (all of its host data is copied).  OED_ENOMEM if its footprint
+ * exceeds the whole budget (it could never be admitted), OED_EINVAL if malformed. */
+int oed_server_submit(oed_server *srv, const oed_request *req, unsigned long long *id);
+/* Current result of request id (status OED_PENDING until it finishes). */
+int oed_server_poll(oed_server *srv, unsigned long long id, oed_result *out);
+/* Wait up to timeout_s seconds for request id; OED_ETIMEOUT if it is still pending. */
+int oed_server_wait(oed_server *srv, unsigned long long id, double timeout_s, oed_result *out);
+/* Device bytes held by running requests, running and queued request counts. */
+int oed_server_stats(oed_server *srv, size_t *in_use, int *active, int *queued);
+/* Cancel queued requests, wait for running ones, stop the workers, free the server. */
+int oed_server_destroy(oed_server *srv);
 
 /* Allocation-free Gauss-Newton Hessian from seismograms the caller already has.
  *

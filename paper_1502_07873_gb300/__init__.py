@@ -18,7 +18,8 @@ from typing import Optional, Sequence
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboed.so")
 
-OED_OK, OED_EINVAL, OED_ENOMEM, OED_ENOTPD, OED_ECUDA, OED_ETIMEOUT = range(6)
+OED_OK, OED_EINVAL, OED_ENOMEM, OED_ENOTPD, OED_ECUDA, OED_ETIMEOUT, OED_PENDING, OED_ECANCELED = range(8)
+OED_SERVER_NO_AUTOTUNE = 1
 OED_FP32, OED_FP64 = 0, 1
 OED_JAC_PAIRS, OED_JAC_DIFFERENCE = 0, 1
 NTHETA = 7
@@ -28,7 +29,9 @@ SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_eig_designs", "oed_nodes_mc", "oed_nodes_smolyak", "oed_eig_host",
            "oed_last_step_time", "oed_autotune", "oed_get_tuning", "oed_set_tuning",
            "oed_resident_min_cluster", "oed_set_jacobian", "oed_get_jacobian",
-           "oed_gauss_newton_noalloc")
+           "oed_gauss_newton_noalloc", "oed_server_create", "oed_server_request_bytes",
+           "oed_server_submit", "oed_server_poll", "oed_server_wait", "oed_server_stats",
+           "oed_server_destroy")
 
 
 class OedError(RuntimeError):
@@ -44,6 +47,19 @@ class Problem(ctypes.Structure):
                 ("vs", ctypes.POINTER(ctypes.c_double)), ("rho", ctypes.POINTER(ctypes.c_double)),
                 ("nrec", ctypes.c_int), ("rec_ix", ctypes.POINTER(ctypes.c_int)),
                 ("precision", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("problem", Problem), ("n", ctypes.c_int), ("theta", ctypes.POINTER(ctypes.c_double)),
+                ("w", ctypes.POINTER(ctypes.c_double)), ("lo", ctypes.POINTER(ctypes.c_double)),
+                ("hi", ctypes.POINTER(ctypes.c_double)), ("rel_step", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("jacobian", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("eig", ctypes.c_double), ("n_bad", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -82,6 +98,13 @@ def library():
         "oed_set_jacobian": (i, [vp, i]),
         "oed_get_jacobian": (i, [vp]),
         "oed_gauss_newton_noalloc": (i, [vp, i, i, i, i, dp, dp, d, d, vp, vp]),
+        "oed_server_create": (i, [ctypes.POINTER(vp), sz, i, i, i]),
+        "oed_server_request_bytes": (sz, [ctypes.POINTER(Request), i]),
+        "oed_server_submit": (i, [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_ulonglong)]),
+        "oed_server_poll": (i, [vp, ctypes.c_ulonglong, ctypes.POINTER(Result)]),
+        "oed_server_wait": (i, [vp, ctypes.c_ulonglong, d, ctypes.POINTER(Result)]),
+        "oed_server_stats": (i, [vp, ctypes.POINTER(sz), ip, ip]),
+        "oed_server_destroy": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -329,3 +352,73 @@ def oed_gauss_newton_noalloc(g, lo, hi, rel_step: float, sigma: float, H, stream
     return int(library().oed_gauss_newton_noalloc(_ptr(g), n, per_node, nlev, nrec, _darr(lo),
                                                   _darr(hi), float(rel_step), float(sigma), _ptr(H),
                                                   _stream(stream)))
+
+
+def make_request(problem: Problem, theta, w, lo, hi, rel_step: float, sigma: float,
+                 jacobian: int = OED_JAC_PAIRS) -> Request:
+    """Build an oed_request from host arrays (kept alive on the returned object)."""
+    import numpy as np
+    r = Request()
+    r.problem = problem
+    r._keep = [problem]
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 7)
+    wt = np.ascontiguousarray(w, dtype=np.float64)
+    r._th, r._w, r._lo, r._hi = th, wt, _darr(lo), _darr(hi)
+    r.n = th.shape[0]
+    r.theta = th.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    r.w = wt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    r.lo, r.hi = r._lo, r._hi
+    r.rel_step, r.sigma, r.jacobian = float(rel_step), float(sigma), int(jacobian)
+    return r
+
+
+class Server:
+    """oed_server: continuous batching of EIG requests with admission by device footprint."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 4, chunk_nodes: int = 64,
+                 autotune: bool = True):
+        self.handle = ctypes.c_void_p()
+        rc = library().oed_server_create(ctypes.byref(self.handle), int(hbm_budget_bytes),
+                                         int(max_active), int(chunk_nodes),
+                                         0 if autotune else OED_SERVER_NO_AUTOTUNE)
+        if rc != OED_OK:
+            raise OedError(rc, "oed_server_create failed")
+        self.chunk_nodes = int(chunk_nodes)
+
+    def request_bytes(self, req: Request) -> int:
+        return int(library().oed_server_request_bytes(ctypes.byref(req), self.chunk_nodes))
+
+    def submit(self, req: Request) -> int:
+        rid = ctypes.c_ulonglong()
+        rc = library().oed_server_submit(self.handle, ctypes.byref(req), ctypes.byref(rid))
+        if rc != OED_OK:
+            raise OedError(rc, "oed_server_submit")
+        return int(rid.value)
+
+    def poll(self, rid: int) -> Result:
+        out = Result()
+        _check(None, library().oed_server_poll(self.handle, rid, ctypes.byref(out)), "oed_server_poll")
+        return out
+
+    def wait(self, rid: int, timeout_s: float = 600.0) -> Result:
+        out = Result()
+        rc = library().oed_server_wait(self.handle, rid, float(timeout_s), ctypes.byref(out))
+        if rc not in (OED_OK, OED_ETIMEOUT):
+            raise OedError(rc, "oed_server_wait")
+        return out
+
+    def stats(self):
+        b, a, q = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+        library().oed_server_stats(self.handle, ctypes.byref(b), ctypes.byref(a), ctypes.byref(q))
+        return int(b.value), int(a.value), int(q.value)
+
+    def close(self):
+        if self.handle:
+            library().oed_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

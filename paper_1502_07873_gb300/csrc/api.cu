@@ -201,8 +201,11 @@ int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
         return OED_ENOMEM;
     }
     char *base = nullptr;
-    cudaError_t e = cudaMalloc(&base, s.total);
+    cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+    cudaError_t e = cudaMallocAsync((void **)&base, s.total, ctx->own_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->own_stream);
     if (e != cudaSuccess) {
+        cudaStreamDestroy(ctx->own_stream);
         delete ctx;
         return e == cudaErrorMemoryAllocation ? OED_ENOMEM : OED_ECUDA;
     }
@@ -217,9 +220,9 @@ int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
     ctx->d_rows = q; q += s.rows;
     ctx->d_rec = (int *)q; q += s.rec;
     ctx->d_hseg = (double *)q; q += s.hseg;
-    cudaMemset(ctx->d_src, 0, s.src);   // defined descriptors before the first source setup
-    cudaMemcpy(ctx->d_rec, ctx->rec_ix.data(), sizeof(int) * p->nrec, cudaMemcpyHostToDevice);
-    cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+    cudaMemsetAsync(ctx->d_src, 0, s.src, ctx->own_stream);   // defined descriptors before first use
+    cudaMemcpyAsync(ctx->d_rec, ctx->rec_ix.data(), sizeof(int) * p->nrec, cudaMemcpyHostToDevice,
+                    ctx->own_stream);
     cudaEventCreate(&ctx->ev_steps[0]);
     cudaEventCreate(&ctx->ev_steps[1]);
     hessian_init(ctx->own_stream);
@@ -238,7 +241,10 @@ int oed_destroy(oed_ctx *ctx)
 {
     if (!ctx) return OED_OK;
     drop_graphs(ctx);
-    if (ctx->d_u0) cudaFree(ctx->d_u0);   // base of the single workspace allocation
+    if (ctx->d_u0) {   // base of the single workspace allocation
+        cudaFreeAsync(ctx->d_u0, ctx->own_stream);
+        cudaStreamSynchronize(ctx->own_stream);
+    }
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     for (int k = 0; k < 2; k++)
         if (ctx->ev_steps[k]) cudaEventDestroy(ctx->ev_steps[k]);

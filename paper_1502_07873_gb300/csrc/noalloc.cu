@@ -145,9 +145,9 @@ extern "C" int oed_gauss_newton_noalloc(const double *g, int n, int per_node, in
     const int lanes = nq <= 128 ? 128 / nq : 1;
     const int threads = lanes * nq;
     const size_t smem = (size_t)threads * 29 * sizeof(double);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_na_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
+    // fixed limit (the largest block this entry point launches), so concurrent calls agree
+    if (cudaFuncSetAttribute(k_na_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             512 * 29 * (int)sizeof(double)) != cudaSuccess)
         return OED_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
     k_na_partial<<<dim3(n, a.nsub), threads, smem, st>>>(g, a, part);

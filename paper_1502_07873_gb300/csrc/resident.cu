@@ -301,11 +301,22 @@ int resident_cluster_size(const oed_ctx *ctx)
     return 0;
 }
 
+// The kernel's dynamic shared-memory limit is always set to the device's opt-in
+// maximum (launches may use less): a fixed value, so concurrent callers with
+// different grids never lower it under each other.
+static cudaError_t set_smem_limit()
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 int resident_max_active_clusters(const oed_ctx *ctx, int C)
 {
     const ResShape r = resident_shape(ctx->g, C);
     if (!r.C) return 0;
-    cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r.smem);
+    set_smem_limit();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(r.C, 1, 1);
     cfg.blockDim = dim3(r.threads_x, r.threads_y, 1);
@@ -331,7 +342,7 @@ cudaError_t launch_resident(const oed_ctx *ctx, int C, int nsolve, cudaStream_t 
 {
     const ResShape r = resident_shape(ctx->g, C);
     if (!r.C) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r.smem);
+    set_smem_limit();
     ResArgs a;
     a.rows = (const RowCoef<float> *)ctx->d_rows;
     a.src = (const SourceDesc<float> *)ctx->d_src;

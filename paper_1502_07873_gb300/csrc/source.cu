@@ -241,15 +241,15 @@ void launch_rows(oed_ctx *ctx, cudaStream_t s)
         lay[3 * nl + l] = ctx->rho[l];
     }
     double *d_lay = nullptr;
-    cudaMalloc(&d_lay, sizeof(double) * lay.size());
-    cudaMemcpy(d_lay, lay.data(), sizeof(double) * lay.size(), cudaMemcpyHostToDevice);
+    cudaMallocAsync((void **)&d_lay, sizeof(double) * lay.size(), s);
+    cudaMemcpyAsync(d_lay, lay.data(), sizeof(double) * lay.size(), cudaMemcpyHostToDevice, s);
     const int nb = (ctx->g.nz + 127) / 128;
     if (ctx->precision == OED_FP64)
         k_rows<double><<<nb, 128, 0, s>>>(ctx->g, nl, d_lay, (RowCoef<double> *)ctx->d_rows);
     else
         k_rows<float><<<nb, 128, 0, s>>>(ctx->g, nl, d_lay, (RowCoef<float> *)ctx->d_rows);
-    cudaStreamSynchronize(s);
-    cudaFree(d_lay);
+    cudaFreeAsync(d_lay, s);
+    cudaStreamSynchronize(s);   // the host vector `lay` must outlive the copy
 }
 
 void launch_sources(const oed_ctx *ctx, const double *theta_nodes, int nnode, int per_node,
