@@ -65,6 +65,26 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Seed of a rank's node batch: every rank evaluates its own independent batch."""
+    return base_seed + 7919 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (all ranks get it); identity without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, steps: int, max_ms: float) -> float:
+    """Whole-job EIG evaluations per second: all ranks' evaluations over the slowest time."""
+    return world * steps / (max_ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -252,7 +272,7 @@ def run_ours(args, rank, world, local):
     nsolve = 15 * w.n_nodes
     ctx = P.Context(P.problem_from_workload(w, prec), max_solves=nsolve)
     # each rank evaluates its own independent batch of nodes (weak scaling)
-    u = w.uniforms(seed=w.seed + 7919 * rank)
+    u = w.uniforms(seed=rank_seed(w.seed, rank))
     lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
     theta = torch.tensor(lo + (hi - lo) * u, dtype=torch.float64, device=dev)
     wt = torch.full((w.n_nodes,), 1.0 / w.n_nodes, dtype=torch.float64, device=dev)
@@ -295,12 +315,8 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
     for k in range(args.steps):
         step_ms.append(ev[k].elapsed_time(ev[k + 1]))
-    total_ms = ev[0].elapsed_time(ev[args.steps])
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[args.steps]), dist, dev)
     eig_val = float(eig.item())
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
 
     # end to end through the host-buffer entry point (pinned inputs, H2D + D2H inside)
     e2e = None
@@ -313,12 +329,8 @@ def run_ours(args, rank, world, local):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e_h, _, _ = P.oed_eig_host(ctx, th_h, w_h, w.prior_lo, w.prior_hi, w.rel_step, sigma)
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * args.steps / el, "unit": "EIG evals/s",
+        el = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": weak_scaling_value(world, args.steps, el * 1e3), "unit": "EIG evals/s",
                "h2d_bytes_per_step": int(th_h.numel() * 8 + w_h.numel() * 8),
                "d2h_bytes_per_step": 8 + 4}
 
@@ -337,13 +349,9 @@ def run_ours(args, rank, world, local):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-        dms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([dms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dms = float(t.item())
+        dms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         eig_d = float(eig.item())
-        diff = {"value": world * args.steps / (dms * 1e-3), "unit": "EIG evals/s",
+        diff = {"value": weak_scaling_value(world, args.steps, dms), "unit": "EIG evals/s",
                 "ms_per_step": dms / args.steps, "solves_per_gpu": 7 * w.n_nodes, "eig": eig_d,
                 "rel_diff_vs_pairs": abs(eig_d - eig_val) / abs(eig_val),
                 "stencil_kernel": ("cluster-resident, %d CTAs per solve" % dtun[0]) if dtun[0]
@@ -385,7 +393,7 @@ def run_ours(args, rank, world, local):
                     "traffic": (tb * per_launch_cells if tb is not None else None),
                     "launch_ms": st_ms}
         launches_per_step = w.nsteps + 5
-    value = world * args.steps / (total_ms * 1e-3)
+    value = weak_scaling_value(world, args.steps, total_ms)
     cb = None
     if not args.no_cpu_baseline and world == 1:
         cb, _ = cpu_baseline(w, sigma, max(1, args.cpu_sample_nodes))
