@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "plain_small"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "plain_small", "layered", "design_sweep"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -435,6 +436,82 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_other_workload(args, rank, world, local):
+    """One EIG evaluation of the layered Smolyak workload (801x401, 3 layers, 4000 steps,
+    589 nodes) or one design sweep (401x201, 2400 steps, 1024 nodes, 40 candidates,
+    3 windows x 5120 designs), FP32 stencil with the difference-form Jacobian."""
+    import torch
+    import paper_1502_07873_gb300 as P
+    from paper_1502_07873_gb300 import build as B
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+    w = W.layered() if args.workload == "layered" else W.design_sweep()
+    sigma = args.sigma if args.sigma > 0 else noise_sigma_gpu(P, torch, w, P.OED_FP32)
+    if args.workload == "layered":
+        x, wt = P.oed_nodes_smolyak(7, w.smolyak_level, w.prior_lo, w.prior_hi)
+        chunk = 7 * 96
+    else:
+        lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+        x = lo + (hi - lo) * w.uniforms(seed=rank_seed(w.seed, rank))
+        wt = np.full(w.n_nodes, 1.0 / w.n_nodes)
+        chunk = 7 * w.n_nodes
+    n = x.shape[0]
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=chunk)
+    ctx.jacobian = P.OED_JAC_DIFFERENCE
+    stream = torch.cuda.current_stream(dev)
+    tuning = ctx.autotune(chunk, stream=stream) if args.tuning == "auto" else \
+        (ctx.set_tuning(*[int(v) for v in args.tuning.split(",")]) or ctx.tuning)
+    theta = torch.tensor(x, device=dev)
+    w_t = torch.tensor(wt, device=dev)
+    H = torch.empty((n, 7, 7), dtype=torch.float64, device=dev)
+    eig = torch.empty(1, dtype=torch.float64, device=dev)
+    if args.workload == "design_sweep":
+        wl = w.win_levels()
+        Hr = torch.empty((n, w.nrec, len(wl), 28), dtype=torch.float64, device=dev)
+        masks = torch.tensor(W.design_subsets(w.nrec, 10, 512, seed=w.seed), device=dev)
+        deig = torch.empty((len(wl), masks.shape[0]), dtype=torch.float64, device=dev)
+
+    def step():
+        if args.workload == "layered":
+            P.oed_hessian(ctx, theta, w.prior_lo, w.prior_hi, w.rel_step, sigma, H, stream=stream)
+            P.oed_eig(ctx, H, w_t, w.prior_lo, w.prior_hi, eig, stream=stream)
+        else:
+            P.oed_hessian(ctx, theta, w.prior_lo, w.prior_hi, w.rel_step, sigma, H, win_levels=wl,
+                          H_rec=Hr, stream=stream)
+            for k in range(len(wl)):
+                P.oed_eig_designs(ctx, Hr, k, masks, w_t, w.prior_lo, w.prior_hi, deig[k], stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    solves = 7 * n
+    cells = w.cells * w.nsteps * solves
+    evals = 1 if args.workload == "layered" else int(deig.numel())
+    out = {"metric": METRIC, "workload": w.name, "value": evals / (ms * 1e-3), "unit": "EIG evals/s",
+           "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "nodes": n, "solves": solves,
+           "gcell_upd_per_s": cells / (ms * 1e-3) / 1e9, "jacobian": "difference",
+           "stencil_kernel": ("cluster-resident, %d CTAs per solve" % tuning[0]) if tuning[0]
+           else "streaming, %d rows/thread, %d warps/block" % (tuning[1], tuning[2]),
+           "clocks": clk.summary()}
+    if args.workload == "layered":
+        out["eig"] = float(eig.item())
+    else:
+        e = deig.cpu().numpy()
+        out["designs_per_window"] = int(masks.shape[0])
+        out["best_design_eig_per_window"] = [float(np.nanmax(r)) for r in e]
+    if rank == 0:
+        print(json.dumps(out))
+
+
 SERVING_GRIDS = ((201, 101, 10.0), (401, 201, 5.0))
 
 
@@ -522,6 +599,9 @@ def main():
     rank, world, local = dist_env()
     if args.serving:
         run_serving(args, rank, world, local)
+        return
+    if args.workload in ("layered", "design_sweep") and args.impl == "ours":
+        run_other_workload(args, rank, world, local)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

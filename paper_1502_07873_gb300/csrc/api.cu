@@ -74,7 +74,7 @@ static Geometry make_geometry(const oed_problem *p)
 }
 
 struct Sizes {
-    size_t u, src, stf, trace, theta, rows, rec, hseg, total;
+    size_t u, src, stf, trace, theta, rows, rec, hseg, err, total;
 };
 
 static Sizes sizes(const Geometry &g, int precision, int max_solves)
@@ -92,7 +92,8 @@ static Sizes sizes(const Geometry &g, int precision, int max_solves)
     s.rows = al((size_t)g.nz * (precision == OED_FP64 ? sizeof(RowCoef<double>) : sizeof(RowCoef<float>)));
     s.rec = al((size_t)g.nrec * sizeof(int));
     s.hseg = al((size_t)chunk * 16 * g.nrec * 28 * sizeof(double));
-    s.total = 2 * s.u + s.src + s.stf + s.trace + s.theta + s.rows + s.rec + s.hseg;
+    s.err = 256;
+    s.total = 2 * s.u + s.src + s.stf + s.trace + s.theta + s.rows + s.rec + s.hseg + s.err;
     return s;
 }
 
@@ -220,6 +221,8 @@ int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
     ctx->d_rows = q; q += s.rows;
     ctx->d_rec = (int *)q; q += s.rec;
     ctx->d_hseg = (double *)q; q += s.hseg;
+    ctx->d_err = (int *)q; q += s.err;
+    cudaMemsetAsync(ctx->d_err, 0, s.err, ctx->own_stream);
     cudaMemsetAsync(ctx->d_src, 0, s.src, ctx->own_stream);   // defined descriptors before first use
     cudaMemcpyAsync(ctx->d_rec, ctx->rec_ix.data(), sizeof(int) * p->nrec, cudaMemcpyHostToDevice,
                     ctx->own_stream);
@@ -316,6 +319,22 @@ int oed_autotune(oed_ctx *ctx, int nsolve, void *stream)
                 best = ctx->tune;
             }
         }
+    // TMA streaming kernel (FP32)
+    if (tma_supported(ctx) && tma_prepare(ctx) > 0) {
+        ctx->tune = StepTuning{best.zs, best.wz, -1};
+        const int probe = nrep < ctx->g.nsteps ? nrep : ctx->g.nsteps;
+        cudaError_t e = launch_steps_tma(ctx, nsolve, st, e0, e1, 2);   // warm
+        if (e == cudaSuccess) e = launch_steps_tma(ctx, nsolve, st, e0, e1, probe);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) return fail(e);
+        ms /= probe;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = ctx->tune;
+        }
+    }
     // cluster-resident kernel (FP32 grids whose two levels fit in 1..8 CTAs)
     const int cmin = resident_cluster_size(ctx);
     if (cmin > 0) {
@@ -357,7 +376,10 @@ int oed_set_tuning(oed_ctx *ctx, int cluster_size, int rows_per_thread, int warp
     if ((rows_per_thread != 2 && rows_per_thread != 4 && rows_per_thread != 8) ||
         (warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8))
         return set_err(ctx, OED_EINVAL, "oed_set_tuning: rows 2/4/8, warps 1/2/4/8");
-    if (cluster_size != 0) {
+    if (cluster_size == -1) {
+        if (!tma_supported(ctx) || tma_prepare(ctx) < 1)
+            return set_err(ctx, OED_EINVAL, "oed_set_tuning: the TMA kernel needs FP32");
+    } else if (cluster_size != 0) {
         const int cmin = resident_cluster_size(ctx);
         if (cmin == 0 || cluster_size < cmin || cluster_size > 8 ||
             resident_max_active_clusters(ctx, cluster_size) < 1)

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(512) k_hsub(const real *__restrict__ trace, Ge
 template <typename real>
 __global__ void k_hcombine(const double *__restrict__ hsub, Geometry g, double s2, int nwin, HArgs a,
                            int per_node, const SourceDesc<real> *__restrict__ src, double *__restrict__ H,
-                           double *__restrict__ H_rec, int *__restrict__ status)
+                           double *__restrict__ H_rec, int *__restrict__ status,
+                           const int *__restrict__ err)
 {
     const int node = blockIdx.x;
     const int nrec = g.nrec;
@@ -89,7 +90,7 @@ __global__ void k_hcombine(const double *__restrict__ hsub, Geometry g, double s
     if (threadIdx.x == 0) {
         int o = 1;
         for (int p = 0; p < per_node; p++) o &= src[(size_t)node * per_node + p].ok;
-        ok = o;
+        ok = *err ? -1 : o;   // -1: a bounded wait in the time loop expired
     }
     __syncthreads();
     const double nan = __longlong_as_double(0x7ff8000000000000ULL);
@@ -102,7 +103,7 @@ __global__ void k_hcombine(const double *__restrict__ hsub, Geometry g, double s
             run += hsub[(((size_t)node * nsub + sub) * nrec + r) * 28 + k];
             while (next < nwin && a.win_sub_end[next] == sub + 1) {
                 if (H_rec)
-                    H_rec[(((size_t)node * nrec + r) * nwin + next) * 28 + k] = ok ? s2 * run : nan;
+                    H_rec[(((size_t)node * nrec + r) * nwin + next) * 28 + k] = ok == 1 ? s2 * run : nan;
                 next++;
             }
         }
@@ -121,9 +122,9 @@ __global__ void k_hcombine(const double *__restrict__ hsub, Geometry g, double s
         const int x = threadIdx.x / 7, y = threadIdx.x % 7;
         const int a0 = x < y ? x : y, b0 = x < y ? y : x;
         const int k = a0 * 7 - a0 * (a0 - 1) / 2 + (b0 - a0);
-        H[(size_t)node * 49 + threadIdx.x] = ok ? s2 * tot[k] : nan;
+        H[(size_t)node * 49 + threadIdx.x] = ok == 1 ? s2 * tot[k] : nan;
     }
-    if (threadIdx.x == 0 && status) status[node] = ok ? 0 : OED_EINVAL;
+    if (threadIdx.x == 0 && status) status[node] = ok == 1 ? 0 : (ok < 0 ? OED_ETIMEOUT : OED_EINVAL);
 }
 
 int hsub_threads(int nrec);
@@ -178,11 +179,11 @@ void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double s
     if (ctx->precision == OED_FP64)
         k_hcombine<double><<<nnode, 256, 0, st>>>(ctx->d_hseg, g, s2, nwin, a, per_node,
                                                   (const SourceDesc<double> *)ctx->d_src, H, H_rec,
-                                                  status);
+                                                  status, ctx->d_err);
     else
         k_hcombine<float><<<nnode, 256, 0, st>>>(ctx->d_hseg, g, s2, nwin, a, per_node,
                                                  (const SourceDesc<float> *)ctx->d_src, H, H_rec,
-                                                 status);
+                                                 status, ctx->d_err);
 }
 
 int hsub_threads(int nrec)

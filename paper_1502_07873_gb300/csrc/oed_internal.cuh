@@ -68,7 +68,8 @@ struct Geometry {
 struct StepTuning {
     int zs;      // streaming kernel: rows marched per thread
     int wz;      // streaming kernel: warps along z in a block
-    int C;       // > 0: cluster-resident kernel with clusters of C CTAs (FP32 only)
+    int C;       // > 0: cluster-resident kernel with clusters of C CTAs (FP32 only);
+                 // -1: TMA streaming kernel (FP32 only); 0: register streaming kernel
 };
 
 }  // namespace oed
@@ -84,6 +85,7 @@ struct oed_ctx {
     // device workspace
     void *d_rows = nullptr;    // RowCoef<real>[nz]
     int *d_rec = nullptr;      // [nrec]
+    int *d_err = nullptr;      // device flag: a bounded wait in a kernel expired
     void *d_u0 = nullptr;      // wavefield level buffer A [max_solves][2][nz][xp]
     void *d_u1 = nullptr;      // wavefield level buffer B
     void *d_src = nullptr;     // SourceDesc<real>[max_solves]
@@ -95,6 +97,7 @@ struct oed_ctx {
     size_t bytes = 0;
     oed::StepTuning tune{4, 4, 0};
     int jac_mode = OED_JAC_PAIRS;   // Jacobian form of oed_hessian
+    int tma_ctas = 0;               // persistent grid of the TMA streaming kernel
     // host-path staging
     cudaStream_t own_stream = nullptr;
     double *h_stage_theta = nullptr, *h_stage_w = nullptr, *h_stage_H = nullptr,
@@ -127,6 +130,12 @@ void launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t s, cudaEv
 void launch_trace_to_f64(const oed_ctx *ctx, int nsolve, double *g, cudaStream_t s);
 void launch_step_probe(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st, cudaEvent_t ev0,
                        cudaEvent_t ev1);
+
+// stream_tma.cu
+bool tma_supported(const oed_ctx *ctx);
+int tma_prepare(oed_ctx *ctx);
+cudaError_t launch_steps_tma(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0,
+                             cudaEvent_t ev1, int nsteps_override);
 
 // resident.cu
 int resident_cluster_size(const oed_ctx *ctx);

@@ -202,20 +202,39 @@ __global__ void __launch_bounds__(768, 1) k_resident(ResArgs a)
                 OED_ROTATE();
                 l++;
             }
-            // rows whose lower neighbour is a local row and that are not the bottom row
+            // rows whose lower neighbour is a local row and that are not the bottom row:
+            // unrolled by three with the three window rows taking turns (no register
+            // moves), pointers advanced by one row per step
             const int lstop = min(l1, nrows - 1);
-#pragma unroll 2
-            for (; l < lstop; l++) {
-                row4_local(cx + (l + 1) * xp, c, cm, cp2, xs);
-                row4_local(cz + (l + 1) * xp, c, cm, cp2, zs);
-                const RowCoef<float> Rc = coef[l];
-                float2 *px = reinterpret_cast<float2 *>(nxb + l * xp + c);
-                float2 *pz = reinterpret_cast<float2 *>(nzb + l * xp + c);
-                float2 ux = *px, uz = *pz;
-                pair_update<false, false>(Rc, xn, xc, xs, zn, zc, zs, ux, uz, sideA, sideB);
-                *px = ux;
-                *pz = uz;
-                OED_ROTATE();
+            {
+                const float *sx = cx + (l + 1) * xp, *sz = cz + (l + 1) * xp;
+                float *ox = nxb + l * xp + c, *oz = nzb + l * xp + c;
+                const RowCoef<float> *cf = coef + l;
+                auto row = [&](const float *an, const float *ac, float *as, const float *bn,
+                               const float *bc, float *bs) {
+                    row4_local(sx, c, cm, cp2, as);
+                    row4_local(sz, c, cm, cp2, bs);
+                    const RowCoef<float> Rc = *cf;
+                    float2 ux = *reinterpret_cast<float2 *>(ox), uz = *reinterpret_cast<float2 *>(oz);
+                    pair_update<false, false>(Rc, an, ac, as, bn, bc, bs, ux, uz, sideA, sideB);
+                    *reinterpret_cast<float2 *>(ox) = ux;
+                    *reinterpret_cast<float2 *>(oz) = uz;
+                    sx += xp;
+                    sz += xp;
+                    ox += xp;
+                    oz += xp;
+                    cf++;
+                };
+                for (; l + 3 <= lstop; l += 3) {
+                    row(xn, xc, xs, zn, zc, zs);   // window (n, c, s)
+                    row(xc, xs, xn, zc, zs, zn);   // window (c, s, n): row l+2 lands in n
+                    row(xs, xn, xc, zs, zn, zc);   // window (s, n, c): row l+3 lands in c
+                }
+                // the loop left rows (l-1, l) in (xn, xc) again; up to two more rows
+                for (; l < lstop; l++) {
+                    row(xn, xc, xs, zn, zc, zs);
+                    OED_ROTATE();
+                }
             }
             // what is left: a last interior row whose lower neighbour sits in CTA rank+1,
             // or the absorbing bottom row

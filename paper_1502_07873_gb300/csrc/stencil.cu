@@ -230,6 +230,13 @@ void launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaE
     const size_t bytes = (size_t)nsolve * ctx->g.solve_stride * ctx->elem;
     cudaMemsetAsync(ctx->d_u0, 0, bytes, st);
     cudaMemsetAsync(ctx->d_u1, 0, bytes, st);
+    if (ctx->tune.C == -1) {
+        launch_steps_tma(ctx, nsolve, st, ev0, ev1, 0);
+        const float *last = (const float *)((ctx->g.nsteps & 1) ? ctx->d_u1 : ctx->d_u0);
+        k_gather<float><<<nsolve, 128, 0, st>>>(last, (float *)ctx->d_trace, ctx->d_rec, ctx->g,
+                                                ctx->g.nsteps, nsolve);
+        return;
+    }
     if (ctx->precision == OED_FP64)
         launch_steps<double>(ctx, nsolve, st, ev0, ev1);
     else

@@ -238,6 +238,39 @@ def test_difference_jacobian_matches_oracle(P, oracle, prec, tol_h, tol_d):
         assert abs(float(dkl[k].item()) - d_ref) <= tol_d * abs(d_ref), (k, float(dkl[k].item()), d_ref)
 
 
+@pytest.mark.parametrize("grid", sorted(GRIDS))
+def test_tma_streaming_kernel_matches_oracle(P, oracle, grid):
+    """The TMA-pipelined streaming kernel (halo tiles by cp.async.bulk.tensor into an
+    mbarrier ring) against the oracle and the register streaming kernel."""
+    w = W.tiny(**GRIDS[grid])
+    th = _thetas(w, 5, seed=31)
+    G = oracle.Grid.from_workload(w)
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=35)
+    g_ref = torch.empty((5, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
+    P.oed_forward(ctx, _t(th), g_ref)
+    ctx.set_tuning(-1, 4, 4)
+    assert ctx.tuning[0] == -1
+    g = torch.empty_like(g_ref)
+    P.oed_forward(ctx, _t(th), g)
+    torch.cuda.synchronize()
+    for k in range(5):
+        out = g[k].cpu().numpy()
+        assert _normwise(out, oracle.forward(G, th[k])) <= 1e-4
+        assert _normwise(out, g_ref[k].cpu().numpy()) <= 1e-5
+    ctx.jacobian = P.OED_JAC_DIFFERENCE
+    H = torch.empty((5, 7, 7), dtype=torch.float64, device=DEV)
+    st = torch.full((5,), -1, dtype=torch.int32, device=DEV)
+    sigma = 0.05
+    P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, sigma, H, status=st)
+    assert st.cpu().tolist() == [0] * 5
+    lp = oracle.log_uniform_density(w.prior_lo, w.prior_hi)
+    for k in range(2):
+        Href, _ = oracle.node_hessian(G, th[k], w.prior_lo, w.prior_hi, w.rel_step, sigma)
+        ld, _, _ = oracle.scaled_logdet(Href)
+        ldg, _, ok = oracle.scaled_logdet(H[k].cpu().numpy())
+        assert ok and abs(oracle.dkl(ldg, 7, lp) - oracle.dkl(ld, 7, lp)) <= 1e-4 * abs(oracle.dkl(ld, 7, lp))
+
+
 def test_resident_rejects_grids_that_do_not_fit(P):
     w = W.tiny(nx=801, nz=401, h=2.5, nsteps=2, nrec=3)
     ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=15)
