@@ -19,6 +19,7 @@
  *   ref_forward        seismograms g_r(t_m)                   (Eq. forward_model)
  *   ref_node_hessian   central-FD Jacobian and H_1            (Eq. H1, Eq. H1_numerics,
  *                      Appendix C)
+ *   ref_node_hessian_sens  H_I from sensitivity solves        (Alg. 1 steps 1-5)
  *   ref_scaled_logdet  S = sqrt(diag H_1), S^-T H_1 S^-1      (Sec. 3.3.3)
  *   ref_dkl            D_KL-hat                               (Thm 4, Eq. DKL_hat)
  *   ref_eig            sum_i w_i D_KL-hat(theta_i)            (Eqs. intpoly, mcs)
@@ -80,6 +81,30 @@ void ref_delta_1d(double a, double h, double *d, double *dp)
     dp[3] = (-2.0 / 3.0 - 4.0 * a / 3.0 + a2 / 2.0 - 23.0 * a3 / 3.0 - 10.0 * R) / h2;
     dp[4] = (1.0 / 12.0 + a / 12.0 - a2 / 4.0 + 4.0 * a3 + 5.0 * R) / h2;
     dp[5] = (-5.0 * a3 / 6.0 - R) / h2;
+}
+
+/* Derivatives of the delta / delta' weights with respect to the source position
+ * x_s (Alg. 1 step 2: the forcing of a sensitivity solve is df/dtheta_j).  With
+ * alpha = (x_s - x_k)/h, d/dx_s = (1/h) d/dalpha applied to each printed
+ * polynomial; P'(alpha) and R'(alpha) are the derivatives of P and R. */
+void ref_delta_1d_dxs(double a, double h, double *dd, double *ddp)
+{
+    double a2 = a * a, a3 = a2 * a, a4 = a3 * a, a5 = a4 * a, a6 = a5 * a, a7 = a6 * a, a8 = a7 * a;
+    double Pp = 25.0 * a4 / 3.0 - 7.0 * a5 / 4.0 - 119.0 * a6 / 12.0 + 9.0 * a7 - 9.0 * a8 / 4.0;
+    double Rp = -25.0 * a3 / 3.0 - 15.0 * a4 / 4.0 + 59.0 * a5 / 2.0 - 28.0 * a6 + 8.0 * a7;
+    double h2 = h * h, h3 = h2 * h;
+    dd[0] = (1.0 / 12.0 - a / 12.0 - a2 / 4.0 - 19.0 * a3 / 6.0 + Pp) / h2;
+    dd[1] = (-2.0 / 3.0 + 4.0 * a / 3.0 + a2 / 2.0 + 16.0 * a3 - 5.0 * Pp) / h2;
+    dd[2] = (-5.0 * a / 2.0 - 97.0 * a3 / 3.0 + 10.0 * Pp) / h2;
+    dd[3] = (2.0 / 3.0 + 4.0 * a / 3.0 - a2 / 2.0 + 98.0 * a3 / 3.0 - 10.0 * Pp) / h2;
+    dd[4] = (-1.0 / 12.0 - a / 12.0 + a2 / 4.0 - 33.0 * a3 / 2.0 + 5.0 * Pp) / h2;
+    dd[5] = (10.0 * a3 / 3.0 - Pp) / h2;
+    ddp[0] = (1.0 / 12.0 + a / 2.0 + 2.0 * a2 + Rp) / h3;
+    ddp[1] = (-4.0 / 3.0 - a - 21.0 * a2 / 2.0 - 5.0 * Rp) / h3;
+    ddp[2] = (5.0 / 2.0 + 22.0 * a2 + 10.0 * Rp) / h3;
+    ddp[3] = (-4.0 / 3.0 + a - 23.0 * a2 - 10.0 * Rp) / h3;
+    ddp[4] = (1.0 / 12.0 - a / 2.0 + 12.0 * a2 + 5.0 * Rp) / h3;
+    ddp[5] = (-5.0 * a2 / 2.0 - Rp) / h3;
 }
 
 /* Gaussian source time function of Sec. 4.1 with omega_0 read as omega_s. */
@@ -283,6 +308,115 @@ int ref_forward(int nx, int nz, double h, double dt, int nsteps, const double *l
     }
     free(ux); free(uz); free(uxm); free(uzm); free(uxn); free(uzn); free(fx); free(fz);
     return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Forward solve driven by a given 6x6 patch (corner i0, j0) and one of three time
+ * functions of (t_s, w_s): kind 0 S(t), kind 1 dS/dt_s = S(t) w^2 (t - t_s),
+ * kind 2 dS/dw_s = S(t) (1/w - w (t - t_s)^2).  Same time stepping as ref_forward.
+ * ------------------------------------------------------------------------- */
+int ref_forward_forcing(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                        const double *mu, const double *nu, int nrec, const int *rec_ix, int i0,
+                        int j0, const double *px, const double *pz, int kind, double ts, double ws,
+                        double *g)
+{
+    ref_grid G = {nx, nz, h, dt, lam, mu, nu};
+    if (i0 < 1 || i0 + 5 > nx - 2 || j0 < 0 || j0 + 5 > nz - 2) return -1;
+    size_t n = (size_t)nx * nz;
+    double *ux = calloc(n, sizeof(double)), *uz = calloc(n, sizeof(double));
+    double *uxm = calloc(n, sizeof(double)), *uzm = calloc(n, sizeof(double));
+    double *uxn = calloc(n, sizeof(double)), *uzn = calloc(n, sizeof(double));
+    double *fx = calloc(n, sizeof(double)), *fz = calloc(n, sizeof(double));
+    for (int r = 0; r < nrec; r++) g[r * 2] = g[r * 2 + 1] = 0.0;
+    for (int m = 0; m < nsteps; m++) {
+        double t = m * dt, sv = ref_stf(t, ts, ws);
+        if (kind == 1) sv = sv * ws * ws * (t - ts);
+        if (kind == 2) sv = sv * (1.0 / ws - ws * (t - ts) * (t - ts));
+        for (int b = 0; b < 6; b++)
+            for (int a = 0; a < 6; a++) {
+                size_t c = (size_t)(j0 + b) * nx + (i0 + a);
+                fx[c] = sv * px[b * 6 + a];
+                fz[c] = sv * pz[b * 6 + a];
+            }
+        ref_step(&G, ux, uz, uxm, uzm, fx, fz, uxn, uzn);
+        double *t2;
+        t2 = uxm; uxm = ux; ux = uxn; uxn = t2;
+        t2 = uzm; uzm = uz; uz = uzn; uzn = t2;
+        for (int r = 0; r < nrec; r++) {
+            g[((size_t)(m + 1) * nrec + r) * 2 + 0] = ux[rec_ix[r]];
+            g[((size_t)(m + 1) * nrec + r) * 2 + 1] = uz[rec_ix[r]];
+        }
+    }
+    free(ux); free(uz); free(uxm); free(uzm); free(uxn); free(uzn); free(fx); free(fz);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * H_I of Alg. 1 steps 1-5 with sensitivity solves: the seismograms of the
+ * solves driven by df/dtheta_j (step 2, analytic derivatives of the discrete
+ * source) are the Jacobian columns J_j (step 3), and
+ * H = sigma^-2 sum_{m,r,c} J^T J (steps 4-5, Eq. H1_numerics).
+ *   x_s, z_s: derivative of the delta / delta' weights; t_s, w_s: derivative of
+ *   S(t); m_xx, m_xz, m_zz: the unit-moment patches.
+ * ------------------------------------------------------------------------- */
+int ref_node_hessian_sens(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                          const double *mu, const double *nu, int nrec, const int *rec_ix,
+                          const double *theta, double sigma, double *H)
+{
+    double xs = theta[0], zs = theta[1], mxx = theta[4], mxz = theta[5], mzz = theta[6];
+    double qx = xs / h, qz = zs / h;
+    int kx = (int)floor(qx), kz = (int)floor(qz);
+    double dx[6], dpx[6], dz[6], dpz[6], ex[6], epx[6], ez[6], epz[6];
+    ref_delta_1d(qx - kx, h, dx, dpx);
+    ref_delta_1d(qz - kz, h, dz, dpz);
+    ref_delta_1d_dxs(qx - kx, h, ex, epx);
+    ref_delta_1d_dxs(qz - kz, h, ez, epz);
+    size_t nrow = (size_t)(nsteps + 1) * nrec * 2;
+    double *gall = malloc(sizeof(double) * nrow * NT);
+    int rc = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : rc) if (!omp_in_parallel())
+#endif
+    for (int j = 0; j < NT; j++) {
+        double px[36], pz[36];
+        int kind = 0;
+        for (int b = 0; b < 6; b++)
+            for (int a = 0; a < 6; a++) {
+                double vx = 0.0, vz = 0.0;
+                if (j == 0) {          /* d/dx_s */
+                    vx = mxx * epx[a] * dz[b] + mxz * ex[a] * dpz[b];
+                    vz = mxz * epx[a] * dz[b] + mzz * ex[a] * dpz[b];
+                } else if (j == 1) {   /* d/dz_s */
+                    vx = mxx * dpx[a] * ez[b] + mxz * dx[a] * epz[b];
+                    vz = mxz * dpx[a] * ez[b] + mzz * dx[a] * epz[b];
+                } else if (j == 2 || j == 3) {   /* time function derivatives */
+                    vx = mxx * dpx[a] * dz[b] + mxz * dx[a] * dpz[b];
+                    vz = mxz * dpx[a] * dz[b] + mzz * dx[a] * dpz[b];
+                    kind = j - 1;
+                } else if (j == 4) {   /* d/dm_xx */
+                    vx = dpx[a] * dz[b];
+                } else if (j == 5) {   /* d/dm_xz */
+                    vx = dx[a] * dpz[b];
+                    vz = dpx[a] * dz[b];
+                } else {               /* d/dm_zz */
+                    vz = dx[a] * dpz[b];
+                }
+                px[b * 6 + a] = vx;
+                pz[b * 6 + a] = vz;
+            }
+        rc |= ref_forward_forcing(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, kx - 2, kz - 2, px,
+                                  pz, kind, theta[2], theta[3], gall + (size_t)j * nrow);
+    }
+    if (rc == 0) {
+        double s2 = 1.0 / (sigma * sigma);
+        for (int a = 0; a < NT * NT; a++) H[a] = 0.0;
+        for (size_t k = 0; k < nrow; k++)
+            for (int a = 0; a < NT; a++)
+                for (int b = 0; b < NT; b++)
+                    H[a * NT + b] += s2 * gall[(size_t)a * nrow + k] * gall[(size_t)b * nrow + k];
+    }
+    free(gall);
+    return rc;
 }
 
 /* ---------------------------------------------------------------------------

@@ -61,6 +61,11 @@ def lib():
         L.ref_node_hessian.argtypes = [c_int, c_int, c_double, c_double, c_int, dp, dp, dp, c_int,
                                        ip, dp, dp, dp, c_double, c_double, c_int, ip, dp, dp]
         L.ref_node_hessian.restype = c_int
+        L.ref_delta_1d_dxs.argtypes = [c_double, c_double, dp, dp]
+        L.ref_delta_1d_dxs.restype = None
+        L.ref_node_hessian_sens.argtypes = [c_int, c_int, c_double, c_double, c_int, dp, dp, dp,
+                                            c_int, ip, dp, c_double, dp]
+        L.ref_node_hessian_sens.restype = c_int
         L.ref_scaled_logdet.argtypes = [dp, dp, dp]
         L.ref_scaled_logdet.restype = c_int
         L.ref_dkl.argtypes = [c_double, c_int, c_double]
@@ -94,6 +99,14 @@ def delta_weights(alpha: float, h: float):
     d = np.zeros(6)
     dp = np.zeros(6)
     lib().ref_delta_1d(float(alpha), float(h), _pd(d), _pd(dp))
+    return d, dp
+
+
+def delta_weights_dxs(alpha: float, h: float):
+    """d/dx_s of the delta and delta' weights (Alg. 1 step 2)."""
+    d = np.zeros(6)
+    dp = np.zeros(6)
+    lib().ref_delta_1d_dxs(float(alpha), float(h), _pd(d), _pd(dp))
     return d, dp
 
 
@@ -188,6 +201,15 @@ def node_hessian(grid: Grid, theta, lo, hi, rel_step, sigma, win_levels=None):
     if rc != 0:
         raise ValueError("source patch leaves the grid interior")
     return H.reshape(7, 7), (Hr.reshape(grid.nrec, nwin, 7, 7) if nwin else None)
+
+
+def node_hessian_sensitivity(grid: Grid, theta, sigma):
+    """H_I (7x7) of Alg. 1 steps 1-5: sensitivity solves driven by df/dtheta_j."""
+    H = np.zeros(49)
+    rc = lib().ref_node_hessian_sens(*grid._args(), _pd(_d(theta)), float(sigma), _pd(H))
+    if rc != 0:
+        raise ValueError("source patch leaves the grid interior")
+    return H.reshape(7, 7)
 
 
 def scaled_logdet(H):
