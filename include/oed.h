@@ -53,6 +53,8 @@ extern "C" {
 #define OED_JAC_PAIRS 0      /* 2 N_theta + 1 solves per node: centre, theta +/- d_j e_j */
 #define OED_JAC_DIFFERENCE 1 /* N_theta solves per node, each driven by the FP64 forcing
                                 difference f(theta + d_j e_j) - f(theta - d_j e_j) */
+#define OED_JAC_SENSITIVITY 2 /* N_theta sensitivity solves per node driven by the
+                                 analytic df/dtheta_j (Alg. 1 steps 1-5) */
 
 #define OED_NTHETA 7
 #define OED_NH 28 /* unique entries of a symmetric 7x7 matrix, row-major upper triangle */
@@ -140,7 +142,13 @@ int oed_set_tuning(oed_ctx *ctx, int cluster_size, int rows_per_thread, int warp
  *    exactly in exact arithmetic; in FP32 it avoids the cancellation of the pairs
  *    form and halves the solves.  Requires 2 d_j < h for j = x_s, z_s (else the
  *    node's status is OED_EINVAL).
- * The node chunk (oed_chunk_nodes) is max_solves / 15 or max_solves / 7. */
+ *  - OED_JAC_SENSITIVITY is Algorithm 1 steps 1-5 of the paper: solve j is driven
+ *    by df/dtheta_j, the analytic derivative of the discrete source (of the
+ *    delta / delta' weights for x_s, z_s; of S(t) for t_s, omega_s; the unit
+ *    moment patches for m_ij), so its seismogram is the Jacobian column itself
+ *    (no step d_j; lo, hi and rel_step are then unused).  It differs from the
+ *    central difference by O(d_j^2).
+ * The node chunk (oed_chunk_nodes) is max_solves / 15 (pairs) or / 7. */
 int oed_set_jacobian(oed_ctx *ctx, int mode);
 int oed_get_jacobian(const oed_ctx *ctx);
 
@@ -256,7 +264,7 @@ typedef struct {
     const double *lo, *hi; /* host [7] prior box */
     double rel_step;       /* FD step as a fraction of the prior width */
     double sigma;          /* noise standard deviation (C_eps = sigma^2 I) */
-    int jacobian;          /* OED_JAC_PAIRS or OED_JAC_DIFFERENCE */
+    int jacobian;          /* OED_JAC_PAIRS, OED_JAC_DIFFERENCE or OED_JAC_SENSITIVITY */
 } oed_request;
 
 typedef struct {

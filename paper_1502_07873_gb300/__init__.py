@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "liboed.so")
 OED_OK, OED_EINVAL, OED_ENOMEM, OED_ENOTPD, OED_ECUDA, OED_ETIMEOUT, OED_PENDING, OED_ECANCELED = range(8)
 OED_SERVER_NO_AUTOTUNE = 1
 OED_FP32, OED_FP64 = 0, 1
-OED_JAC_PAIRS, OED_JAC_DIFFERENCE = 0, 1
+OED_JAC_PAIRS, OED_JAC_DIFFERENCE, OED_JAC_SENSITIVITY = 0, 1, 2
 NTHETA = 7
 
 SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",

@@ -393,8 +393,8 @@ int oed_set_tuning(oed_ctx *ctx, int cluster_size, int rows_per_thread, int warp
 int oed_set_jacobian(oed_ctx *ctx, int mode)
 {
     if (!ctx) return OED_EINVAL;
-    if (mode != OED_JAC_PAIRS && mode != OED_JAC_DIFFERENCE)
-        return set_err(ctx, OED_EINVAL, "oed_set_jacobian: OED_JAC_PAIRS or OED_JAC_DIFFERENCE");
+    if (mode != OED_JAC_PAIRS && mode != OED_JAC_DIFFERENCE && mode != OED_JAC_SENSITIVITY)
+        return set_err(ctx, OED_EINVAL, "oed_set_jacobian: unknown Jacobian form");
     ctx->jac_mode = mode;
     return OED_OK;
 }
@@ -449,7 +449,8 @@ int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, cons
     for (int j = 0; j < kNT; j++) {
         if (!(hi[j] > lo[j])) return set_err(ctx, OED_EINVAL, "oed_hessian: need hi > lo");
         d[j] = rel_step * (hi[j] - lo[j]);
-        inv2d[j] = 1.0 / (2.0 * d[j]);
+        // sensitivity solves give the Jacobian columns directly
+        inv2d[j] = ctx->jac_mode == OED_JAC_SENSITIVITY ? 1.0 : 1.0 / (2.0 * d[j]);
     }
     // segment ends: the window ends (increasing), then all levels
     std::vector<int> seg_end;

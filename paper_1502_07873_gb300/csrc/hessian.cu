@@ -162,7 +162,7 @@ void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double s
     const int threads = hsub_threads(g.nrec);
     const size_t smem = (size_t)threads * 29 * sizeof(double);
     dim3 grid(nnode, nsub);
-    const bool diff = ctx->jac_mode == OED_JAC_DIFFERENCE;
+    const bool diff = ctx->jac_mode != OED_JAC_PAIRS;   // one solve per parameter
     if (ctx->precision == OED_FP64) {
         if (diff)
             k_hsub<double, true><<<grid, threads, smem, st>>>((const double *)ctx->d_trace, g, a, ctx->d_hseg);

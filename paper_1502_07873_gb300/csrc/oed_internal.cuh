@@ -120,7 +120,7 @@ void launch_sources(const oed_ctx *ctx, const double *theta_nodes, int nnode, in
                     const double *step, cudaStream_t s);
 inline int solves_per_node(const oed_ctx *ctx)
 {
-    return ctx->jac_mode == OED_JAC_DIFFERENCE ? kND : kNP;
+    return ctx->jac_mode == OED_JAC_PAIRS ? kNP : kND;
 }
 void launch_rows(oed_ctx *ctx, cudaStream_t s);
 

@@ -70,7 +70,7 @@ struct oed_server {
 static int run_request(oed_server *srv, Request &rq, oed_result *res)
 {
     cudaSetDevice(srv->device);
-    const int per_node = rq.jacobian == OED_JAC_DIFFERENCE ? 7 : 15;
+    const int per_node = rq.jacobian == OED_JAC_PAIRS ? 15 : 7;
     oed_ctx *ctx = nullptr;
     int rc = oed_create(&ctx, &rq.p, per_node * rq.chunk);
     if (rc) return rc;
@@ -187,7 +187,7 @@ int oed_server_create(oed_server **out, size_t hbm_budget_bytes, int max_active,
 size_t oed_server_request_bytes(const oed_request *req, int chunk_nodes)
 {
     if (!req || req->n < 1 || chunk_nodes < 1) return 0;
-    const int per_node = req->jacobian == OED_JAC_DIFFERENCE ? 7 : 15;
+    const int per_node = req->jacobian == OED_JAC_PAIRS ? 15 : 7;
     const int chunk = req->n < chunk_nodes ? req->n : chunk_nodes;
     const size_t ws = oed_workspace_bytes(&req->problem, per_node * chunk);
     if (!ws) return 0;
@@ -198,7 +198,9 @@ int oed_server_submit(oed_server *srv, const oed_request *req, unsigned long lon
 {
     if (!srv || !req || !id || req->n < 1 || !req->theta || !req->w || !req->lo || !req->hi)
         return OED_EINVAL;
-    if (req->jacobian != OED_JAC_PAIRS && req->jacobian != OED_JAC_DIFFERENCE) return OED_EINVAL;
+    if (req->jacobian != OED_JAC_PAIRS && req->jacobian != OED_JAC_DIFFERENCE &&
+        req->jacobian != OED_JAC_SENSITIVITY)
+        return OED_EINVAL;
     Request rq;
     rq.chunk = req->n < srv->chunk_nodes ? req->n : srv->chunk_nodes;
     rq.footprint = oed_server_request_bytes(req, srv->chunk_nodes);

@@ -35,6 +35,27 @@ __device__ void delta_weights(double a, double h, double *d, double *dp)
     dp[5] = (-5.0 / 6.0 * a * a * a - R) * ih2;
 }
 
+// d/dx_s of the six delta and delta' weights (the forcing derivative of a
+// sensitivity solve, Alg. 1 step 2): (1/h) d/dalpha of the printed polynomials.
+__device__ void delta_weights_dxs(double a, double h, double *d, double *dp)
+{
+    const double Pp = a * a * a * a * (25.0 / 3.0 + a * (-7.0 / 4.0 + a * (-119.0 / 12.0 + a * (9.0 - 9.0 / 4.0 * a))));
+    const double Rp = a * a * a * (-25.0 / 3.0 + a * (-15.0 / 4.0 + a * (59.0 / 2.0 + a * (-28.0 + 8.0 * a))));
+    const double ih2 = 1.0 / (h * h), ih3 = ih2 / h;
+    d[0] = (1.0 / 12.0 + a * (-1.0 / 12.0 + a * (-1.0 / 4.0 - 19.0 / 6.0 * a)) + Pp) * ih2;
+    d[1] = (-2.0 / 3.0 + a * (4.0 / 3.0 + a * (1.0 / 2.0 + 16.0 * a)) - 5.0 * Pp) * ih2;
+    d[2] = (a * (-5.0 / 2.0 - 97.0 / 3.0 * a * a) + 10.0 * Pp) * ih2;
+    d[3] = (2.0 / 3.0 + a * (4.0 / 3.0 + a * (-1.0 / 2.0 + 98.0 / 3.0 * a)) - 10.0 * Pp) * ih2;
+    d[4] = (-1.0 / 12.0 + a * (-1.0 / 12.0 + a * (1.0 / 4.0 - 33.0 / 2.0 * a)) + 5.0 * Pp) * ih2;
+    d[5] = (10.0 / 3.0 * a * a * a - Pp) * ih2;
+    dp[0] = (1.0 / 12.0 + a * (1.0 / 2.0 + 2.0 * a) + Rp) * ih3;
+    dp[1] = (-4.0 / 3.0 + a * (-1.0 - 21.0 / 2.0 * a) - 5.0 * Rp) * ih3;
+    dp[2] = (5.0 / 2.0 + 22.0 * a * a + 10.0 * Rp) * ih3;
+    dp[3] = (-4.0 / 3.0 + a * (1.0 - 23.0 * a) - 10.0 * Rp) * ih3;
+    dp[4] = (1.0 / 12.0 + a * (-1.0 / 2.0 + 12.0 * a) + 5.0 * Rp) * ih3;
+    dp[5] = (-5.0 / 2.0 * a * a - Rp) * ih3;
+}
+
 struct FdStep {
     double d[kNT];
 };
@@ -76,7 +97,7 @@ __device__ __forceinline__ double stf_value(double t, double ts, double ws)
 // and the moments the spatial patch differs (the two 6x6 patches are subtracted
 // on their 7x7 union); for j = t_s, omega_s the time function differs.
 template <typename real>
-__global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, int per_node,
+__global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, int per_node, int sens,
                           FdStep step, Geometry g, const RowCoef<real> *__restrict__ rows,
                           SourceDesc<real> *__restrict__ src, real *__restrict__ stf,
                           double *__restrict__ theta_out)
@@ -84,16 +105,18 @@ __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, in
     const int s = blockIdx.x;
     if (s >= nsolve) return;
     const int node = s / per_node, p = s % per_node;
-    const bool diff = per_node == kND;
+    const bool diff = per_node == kND && !sens;
     __shared__ double th[kNT], tp[kNT], tm[kNT];
     __shared__ double w7x[kPatch * kPatch], w7z[kPatch * kPatch];
     __shared__ int corner[3];
     __shared__ int time_diff;
+    __shared__ int time_kind;   // sensitivity solves: 0 S, 1 dS/dt_s, 2 dS/domega_s
     if (threadIdx.x < kNT) {
         const int j = threadIdx.x;
         const double v = theta_nodes[(size_t)node * kNT + j];
         double vs = v;
-        if (!diff && p > 0 && j == (p - 1) / 2) vs += ((p - 1) & 1) ? -step.d[j] : step.d[j];
+        // pairs form: p = 0 centre, p = 1 + 2j: +d_j, p = 2 + 2j: -d_j
+        if (per_node == kNP && p > 0 && j == (p - 1) / 2) vs += ((p - 1) & 1) ? -step.d[j] : step.d[j];
         th[j] = vs;
         tp[j] = v + ((diff && j == p) ? step.d[j] : 0.0);
         tm[j] = v - ((diff && j == p) ? step.d[j] : 0.0);
@@ -106,7 +129,47 @@ __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, in
         int kx = 0, kz = 0, ok;
         int i0, j0, span;   // span: 6 or 7 nodes of the patch actually used
         time_diff = diff && (p == 2 || p == 3);
-        if (!diff || time_diff) {
+        time_kind = (sens && (p == 2 || p == 3)) ? p - 1 : 0;
+        if (sens) {
+            // Alg. 1 step 2: the forcing of solve j is df/dtheta_j of the discrete source
+            const double qx = th[0] / g.h, qz = th[1] / g.h;
+            const double flx = floor(qx), flz = floor(qz);
+            ok = isfinite(qx) && isfinite(qz) && fabs(flx) < 1e9 && fabs(flz) < 1e9;
+            double dx[6], dpx[6], dz[6], dpz[6], ex[6], epx[6], ez[6], epz[6];
+            delta_weights(qx - flx, g.h, dx, dpx);
+            delta_weights(qz - flz, g.h, dz, dpz);
+            delta_weights_dxs(qx - flx, g.h, ex, epx);
+            delta_weights_dxs(qz - flz, g.h, ez, epz);
+            kx = ok ? (int)flx : 0;
+            kz = ok ? (int)flz : 0;
+            i0 = kx - 2;
+            j0 = kz - 2;
+            span = 6;
+            const double mxx = th[4], mxz = th[5], mzz = th[6];
+            for (int b = 0; b < 6; b++)
+                for (int a2 = 0; a2 < 6; a2++) {
+                    double vx = 0.0, vz = 0.0;
+                    if (p == 0) {
+                        vx = mxx * epx[a2] * dz[b] + mxz * ex[a2] * dpz[b];
+                        vz = mxz * epx[a2] * dz[b] + mzz * ex[a2] * dpz[b];
+                    } else if (p == 1) {
+                        vx = mxx * dpx[a2] * ez[b] + mxz * dx[a2] * epz[b];
+                        vz = mxz * dpx[a2] * ez[b] + mzz * dx[a2] * epz[b];
+                    } else if (p == 2 || p == 3) {
+                        vx = mxx * dpx[a2] * dz[b] + mxz * dx[a2] * dpz[b];
+                        vz = mxz * dpx[a2] * dz[b] + mzz * dx[a2] * dpz[b];
+                    } else if (p == 4) {
+                        vx = dpx[a2] * dz[b];
+                    } else if (p == 5) {
+                        vx = dx[a2] * dpz[b];
+                        vz = dpx[a2] * dz[b];
+                    } else {
+                        vz = dx[a2] * dpz[b];
+                    }
+                    w7x[b * kPatch + a2] = vx;
+                    w7z[b * kPatch + a2] = vz;
+                }
+        } else if (!diff || time_diff) {
             ok = source_patch6(th, g.h, &kx, &kz, fx, fz);
             i0 = kx - 2;
             j0 = kz - 2;
@@ -154,8 +217,10 @@ __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, in
     }
     for (int m = threadIdx.x; m < g.nsteps; m += blockDim.x) {
         const double t = m * g.dt;
-        const double v = time_diff ? stf_value(t, tp[2], tp[3]) - stf_value(t, tm[2], tm[3])
-                                   : stf_value(t, th[2], th[3]);
+        double v = time_diff ? stf_value(t, tp[2], tp[3]) - stf_value(t, tm[2], tm[3])
+                             : stf_value(t, th[2], th[3]);
+        if (time_kind == 1) v *= th[3] * th[3] * (t - th[2]);                 // dS/dt_s
+        if (time_kind == 2) v *= 1.0 / th[3] - th[3] * (t - th[2]) * (t - th[2]);   // dS/domega_s
         stf[(size_t)s * g.nsteps + m] = (real)v;
     }
 }
@@ -255,17 +320,18 @@ void launch_rows(oed_ctx *ctx, cudaStream_t s)
 void launch_sources(const oed_ctx *ctx, const double *theta_nodes, int nnode, int per_node,
                     const double *step, cudaStream_t s)
 {
+    const int sens = (per_node == kND && ctx->jac_mode == OED_JAC_SENSITIVITY) ? 1 : 0;
     FdStep st;
     for (int j = 0; j < kNT; j++) st.d[j] = step ? step[j] : 0.0;
     const int nsolve = nnode * per_node;
     if (nsolve <= 0) return;
     if (ctx->precision == OED_FP64)
         k_sources<double><<<nsolve, 128, 0, s>>>(
-            theta_nodes, nsolve, per_node, st, ctx->g, (const RowCoef<double> *)ctx->d_rows,
+            theta_nodes, nsolve, per_node, sens, st, ctx->g, (const RowCoef<double> *)ctx->d_rows,
             (SourceDesc<double> *)ctx->d_src, (double *)ctx->d_stf, ctx->d_theta);
     else
         k_sources<float><<<nsolve, 128, 0, s>>>(
-            theta_nodes, nsolve, per_node, st, ctx->g, (const RowCoef<float> *)ctx->d_rows,
+            theta_nodes, nsolve, per_node, sens, st, ctx->g, (const RowCoef<float> *)ctx->d_rows,
             (SourceDesc<float> *)ctx->d_src, (float *)ctx->d_stf, ctx->d_theta);
 }
 

@@ -271,6 +271,32 @@ def test_tma_streaming_kernel_matches_oracle(P, oracle, grid):
         assert ok and abs(oracle.dkl(ldg, 7, lp) - oracle.dkl(ld, 7, lp)) <= 1e-4 * abs(oracle.dkl(ld, 7, lp))
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+def test_sensitivity_jacobian_matches_oracle(P, oracle, prec):
+    """Algorithm 1 steps 1-5 (sensitivity solves driven by the analytic df/dtheta_j) against
+    the oracle's own sensitivity H_I: FP64 to 1e-9 (scaled), FP32 D_KL-hat to 1e-4."""
+    w = W.tiny(**GRIDS["layered_70x41"])
+    th = _thetas(w, 3, seed=41)
+    G = oracle.Grid.from_workload(w)
+    sigma = 0.05
+    ctx = P.Context(P.problem_from_workload(w, prec), max_solves=21)
+    ctx.jacobian = P.OED_JAC_SENSITIVITY
+    assert ctx.chunk_nodes == 3
+    H = torch.empty((3, 7, 7), dtype=torch.float64, device=DEV)
+    st = torch.empty(3, dtype=torch.int32, device=DEV)
+    P.oed_hessian(ctx, _t(th), w.prior_lo, w.prior_hi, w.rel_step, sigma, H, status=st)
+    assert st.cpu().tolist() == [0, 0, 0]
+    lp = oracle.log_uniform_density(w.prior_lo, w.prior_hi)
+    for k in range(3):
+        Hs = oracle.node_hessian_sensitivity(G, th[k], sigma)
+        if prec == 1:
+            assert _scaled(H[k].cpu().numpy(), Hs) <= 1e-9
+        ld, _, _ = oracle.scaled_logdet(Hs)
+        ldg, _, ok = oracle.scaled_logdet(H[k].cpu().numpy())
+        d_ref = oracle.dkl(ld, 7, lp)
+        assert ok and abs(oracle.dkl(ldg, 7, lp) - d_ref) <= 1e-4 * abs(d_ref)
+
+
 def test_resident_rejects_grids_that_do_not_fit(P):
     w = W.tiny(nx=801, nz=401, h=2.5, nsteps=2, nrec=3)
     ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=15)
