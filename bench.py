@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "plain_small", "layered", "design_sweep"])
+                    choices=["batched", "plain_small", "layered", "design_sweep", "paper_scenarios"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -512,6 +512,71 @@ def run_other_workload(args, rank, world, local):
         print(json.dumps(out))
 
 
+def run_paper_scenarios(args, rank, world, local):
+    """The paper's model problem (Sec. 4.1: two layers, h = 200 m, dt = 0.025 s, T = 8 s,
+    C_eps = 1e-4 I) and its Scenarios I-III (Sec. 4.5): per-receiver partial Hessians over
+    the 91 candidate surface nodes from sensitivity solves (Alg. 1 steps 1-5), then the EIG
+    of all 36 designs, for the sparse grid of 8583 nodes and M = 10^4 MC nodes."""
+    import torch
+    import paper_1502_07873_gb300 as P
+    from paper_1502_07873_gb300 import build as B
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+    w = W.paper_model()
+    sigma = 0.01
+    scen = W.paper_scenarios()
+    masks = torch.tensor(np.stack([m for _, _, m in scen]), device=dev)
+    chunk = 2048
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=7 * chunk)
+    ctx.jacobian = P.OED_JAC_SENSITIVITY
+    stream = torch.cuda.current_stream(dev)
+    tuning = ctx.autotune(7 * chunk, stream=stream)
+    rules = {}
+    x, wt = P.oed_nodes_smolyak(7, 5, w.prior_lo, w.prior_hi)
+    rules["sparse_grid_8583"] = (x, wt)
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+    u = np.random.default_rng(6).random((10000, 7))
+    rules["monte_carlo_10000"] = (lo + (hi - lo) * u, np.full(10000, 1e-4))
+    out = {"metric": "paper model problem, Scenarios I-III (Sec. 4.5)", "workload": w.name,
+           "jacobian": "sensitivity (Alg. 1 steps 1-5)", "sigma": sigma,
+           "stencil_kernel": ("cluster-resident, %d CTAs per solve" % tuning[0]) if tuning[0]
+           else "streaming", "rules": {}}
+    for name, (x, wt) in rules.items():
+        n = x.shape[0]
+        th = torch.tensor(x, device=dev)
+        w_t = torch.tensor(wt, device=dev)
+        H = torch.empty((n, 7, 7), dtype=torch.float64, device=dev)
+        Hr = torch.empty((n, w.nrec, 1, 28), dtype=torch.float64, device=dev)
+        eig = torch.empty(len(scen), dtype=torch.float64, device=dev)
+        nb = torch.empty(len(scen), dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.oed_hessian(ctx, th, w.prior_lo, w.prior_hi, w.rel_step, sigma, H, win_levels=[w.nlevels],
+                      H_rec=Hr, stream=stream)
+        P.oed_eig_designs(ctx, Hr, 0, masks, w_t, w.prior_lo, w.prior_hi, eig, n_bad=nb, stream=stream)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e = eig.cpu().numpy()
+        b = nb.cpu().numpy()
+        res = {"nodes": n, "solves": 7 * n, "seconds": el, "designs": len(scen),
+               "cell_updates": w.cells * w.nsteps * 7 * n}
+        for sc in ("I", "II", "III"):
+            res[f"scenario_{sc}"] = [[v, float(e[k]), int(b[k])] for k, (s_, v, _) in enumerate(scen) if s_ == sc]
+        out["rules"][name] = res
+    # conditioning at the prior mean (Sec. 4.2 prints 3.88e30 unscaled and 12.16 scaled)
+    th = torch.tensor(np.array([W.PAPER_PRIOR_MEAN]), device=dev)
+    H = torch.empty((1, 7, 7), dtype=torch.float64, device=dev)
+    P.oed_hessian(ctx, th, w.prior_lo, w.prior_hi, w.rel_step, sigma, H, stream=stream)
+    Hm = H[0].cpu().numpy()
+    S = np.sqrt(np.diag(Hm))
+    out["prior_mean_cond"] = {"unscaled": float(np.linalg.cond(Hm)),
+                              "scaled": float(np.linalg.cond(Hm / np.outer(S, S))),
+                              "receivers": "all 91 candidates"}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 SERVING_GRIDS = ((201, 101, 10.0), (401, 201, 5.0))
 
 
@@ -599,6 +664,9 @@ def main():
     rank, world, local = dist_env()
     if args.serving:
         run_serving(args, rank, world, local)
+        return
+    if args.workload == "paper_scenarios" and args.impl == "ours":
+        run_paper_scenarios(args, rank, world, local)
         return
     if args.workload in ("layered", "design_sweep") and args.impl == "ours":
         run_other_workload(args, rank, world, local)

@@ -457,6 +457,31 @@ def test_monte_carlo_nodes(oracle):
     assert np.all(th >= np.array(w.prior_lo)) and np.all(th <= np.array(w.prior_hi))
 
 
+def _golden_cond():
+    vals = {}
+    with open(os.path.join(HERE, "golden", "scaled_hessian_cond.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_paper_model_conditioning_matches_sec_4_2(oracle):
+    """The paper's worked example (Sec. 4.2): at the prior mean of its model problem,
+    cond(H_1) = 3.88e30 and, after scaling by sqrt(diag H_1), 12.16.  The oracle reproduces
+    both within 5% (central-FD and sensitivity Jacobians alike)."""
+    gold = _golden_cond()
+    w = W.paper_model()
+    G = oracle.Grid.from_workload(w)
+    mean = np.array(W.PAPER_PRIOR_MEAN)
+    for H in (oracle.node_hessian(G, mean, w.prior_lo, w.prior_hi, w.rel_step, 0.01)[0],
+              oracle.node_hessian_sensitivity(G, mean, 0.01)):
+        S = np.sqrt(np.diag(H))
+        assert abs(np.linalg.cond(H) / gold["cond_unscaled"] - 1) < 0.05
+        assert abs(np.linalg.cond(H / np.outer(S, S)) / gold["cond_scaled"] - 1) < 0.05
+
+
 def test_small_workload_scaled_hessian_conditioning(oracle):
     """Sec. 4.2: scaling by sqrt(diag H_1) brings cond from ~1e30 to O(10) (the paper prints
     3.88e30 and 12.16 for its own workload)."""

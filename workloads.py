@@ -171,5 +171,48 @@ def tiny(nx=41, nz=21, h=50.0, nsteps=100, nrec=5, n_nodes=2, seed=11, layers=HO
                 n_nodes=n_nodes, seed=seed, **kw)
 
 
+# The paper's own model problem (Sec. 4.1): a two-layer LOH.1-like box
+# [-10000, 10000] x [-15000, 0] m, here shifted to x in [0, 20000] and depth in
+# [0, 15000]; top layer 1000 m thick.  h = 200 m, dt = 0.025 s, T = 8 s (321 levels),
+# C_eps = 1e-4 I (sigma = 0.01).  Priors (Sec. 4.1) in the shifted coordinates.
+PAPER_LAYERS = ((0.0, 4000.0, 2000.0, 2600.0), (1000.0, 6000.0, 3464.0, 2700.0))
+PAPER_PRIOR_LO = (9000.0, 1000.0, 0.5, 3.0, 1e13, 1e13, 1e13)
+PAPER_PRIOR_HI = (11000.0, 3000.0, 1.5, 5.0, 1e15, 1e15, 1e15)
+PAPER_PRIOR_MEAN = (10000.0, 2000.0, 1.0, 4.0, 1e14, 1e14, 1e14)
+
+
+PAPER_CANDIDATES = tuple(range(-9000, 9001, 200))   # x_1 of every candidate receiver
+
+
+def paper_model(n_nodes: int = 0, seed: int = 6) -> Workload:
+    """The paper's model problem with the 91 candidate receivers its scenarios use: every
+    surface node with x_1 in [-9000, 9000] m (x = 1000 .. 19000 m here, 200 m apart)."""
+    h = 200.0
+    return Workload(name="paper_loh_101x76_320steps", nx=101, nz=76, h=h, nsteps=320, dt=0.025,
+                    layers=PAPER_LAYERS, rec_ix=[int((x1 + 10000.0) / h) for x1 in PAPER_CANDIDATES],
+                    prior_lo=PAPER_PRIOR_LO, prior_hi=PAPER_PRIOR_HI, n_nodes=n_nodes, seed=seed)
+
+
+def paper_scenarios():
+    """Receiver designs of Sec. 4.5 as masks over the candidates of paper_model().
+    Returns a list of (scenario, parameter value, mask)."""
+    cand = list(PAPER_CANDIDATES)
+
+    def mask(positions):
+        m = np.zeros(len(cand), dtype=np.uint8)
+        for x in positions:
+            m[cand.index(int(round(x)))] = 1
+        return m
+
+    out = []
+    for nr, dr in zip((3, 5, 9, 17, 41, 81), (8000, 4000, 2000, 1000, 400, 200)):   # Scenario I
+        out.append(("I", nr, mask([(k - (nr - 1) / 2) * dr for k in range(nr)])))
+    for nr in range(1, 20, 2):                                                       # Scenario II
+        out.append(("II", nr, mask([(k - (nr - 1) / 2) * 1000 for k in range(nr)])))
+    for dr in range(200, 4001, 200):                                                 # Scenario III
+        out.append(("III", dr, mask([(k - 2) * dr for k in range(5)])))
+    return out
+
+
 ALL = {"plain_small": plain_small, "batched": batched, "layered": layered,
        "design_sweep": design_sweep}
