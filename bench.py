@@ -32,12 +32,26 @@ import workloads as W  # noqa: E402
 
 METRIC = "EIG evals/s & stencil Gcell-upd/s (% HBM roofline) at rel err<=1e-3; p50/p99"
 BYTES_PER_CELL_UPDATE = {"f32": 24, "f64": 48}   # read u^m, u^{m-1}; write u^{m+1}; 2 comps
-# FP32 operations of one interior node update (both components, Eq. Full_Disc as
-# written in stencil_cell.cuh): 21 per divergence component + 4 per leap-frog update
-FLOPS_PER_CELL_UPDATE = 50
+# FP32 operations of one interior node update as the kernels evaluate it (both
+# components, stencil_cell.cuh, a multiply-add counted as 2): per component the
+# second difference 2.5 (three neighbour differences shared by a column pair), the
+# vertical and cross differences 1 + 1 (each shared with the next row), the operator
+# term 1 multiply + 4 multiply-adds = 9, the leap-frog increment form 3
+FLOPS_PER_CELL_UPDATE = 33
+# FP32 instructions behind those flops (the FP32 pipe's own roofline: 25 per node)
+FP32_INSTR_PER_CELL_UPDATE = 25
 # FP32 peak derived from the unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 (FMA)
 # x 2.07 GHz maximum SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def kernel_label(t):
+    """Human-readable stencil kernel for a (cluster, rows, warps) tuning triple."""
+    if t[0] > 0:
+        return "cluster-resident, %d CTAs per solve" % t[0]
+    if t[0] < 0:
+        return "TMA streaming (persistent, 4-stage mbarrier ring)"
+    return "streaming, %d rows/thread, %d warps/block" % (t[1], t[2])
 
 
 def parse():
@@ -103,7 +117,8 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {"k_resident": ("resident.cu", "stencil_cell.cuh", "oed_internal.cuh"),
-                  "k_step": ("stencil.cu", "stencil_cell.cuh", "oed_internal.cuh")}
+                  "k_step": ("stencil.cu", "stencil_cell.cuh", "oed_internal.cuh"),
+                  "k_step_tma": ("stream_tma.cu", "stencil_cell.cuh", "oed_internal.cuh")}
 
 
 def kernel_sources_hash(kernel: str) -> str:
@@ -355,8 +370,7 @@ def run_ours(args, rank, world, local):
         diff = {"value": weak_scaling_value(world, args.steps, dms), "unit": "EIG evals/s",
                 "ms_per_step": dms / args.steps, "solves_per_gpu": 7 * w.n_nodes, "eig": eig_d,
                 "rel_diff_vs_pairs": abs(eig_d - eig_val) / abs(eig_val),
-                "stencil_kernel": ("cluster-resident, %d CTAs per solve" % dtun[0]) if dtun[0]
-                else "streaming, %d rows/thread, %d warps/block" % (dtun[1], dtun[2])}
+                "stencil_kernel": kernel_label(dtun)}
         ctx.jacobian = P.OED_JAC_PAIRS
 
     if rank != 0:
@@ -382,13 +396,16 @@ def run_ours(args, rank, world, local):
                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                     "algorithmic_flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
+                    "fp32_pipe_frac": FP32_INSTR_PER_CELL_UPDATE * cells / (launch_ms * 1e-3)
+                    / (FP32_PEAK_TFLOPS * 1e12 / 2),
                     "traffic": (tb * cells if tb is not None else None), "launch_ms": launch_ms,
                     "hbm_equivalent": {"gbs": hbm_equiv, "frac_of_measured_hbm": hbm_equiv / peak,
                                        "note": "24 B per cell-update a streaming kernel would move"}}
         launches_per_step = 5
     else:
-        tb = ncu_traffic("k_step")
-        roofline = {"bound": "hbm", "kernel": "k_step (streaming leap-frog, one step)",
+        kname = "k_step_tma" if tuning[0] < 0 else "k_step"
+        tb = ncu_traffic(kname)
+        roofline = {"bound": "hbm", "kernel": kname + " (streaming leap-frog, one step)",
                     "achieved": hbm_equiv, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                     "frac": hbm_equiv / peak, "algorithmic_bytes_per_cell_update": bpc,
                     "traffic": (tb * per_launch_cells if tb is not None else None),
@@ -415,8 +432,7 @@ def run_ours(args, rank, world, local):
                                 "+/- seismograms" if args.jacobian == "pairs" else
                                 "7 solves per node driven by FP64 forcing differences")),
                    "parallelism": f"replicas x{world} (independent node batches)",
-                   "stencil_kernel": ("cluster-resident, %d CTAs per solve" % tuning[0]) if tuning[0]
-                   else "streaming, %d rows/thread, %d warps/block" % (tuning[1], tuning[2]),
+                   "stencil_kernel": kernel_label(tuning),
                    "l2": "no flush: 5.1 GB of wavefields per step exceed the 129 MB L2"},
         "gcell_upd_per_s": world * cells * args.steps / (total_ms * 1e-3) / 1e9,
         "stencil_gcell_upd_per_s": per_launch_cells / (st_ms * 1e-3) / 1e9,
@@ -499,8 +515,7 @@ def run_other_workload(args, rank, world, local):
     out = {"metric": METRIC, "workload": w.name, "value": evals / (ms * 1e-3), "unit": "EIG evals/s",
            "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "nodes": n, "solves": solves,
            "gcell_upd_per_s": cells / (ms * 1e-3) / 1e9, "jacobian": "difference",
-           "stencil_kernel": ("cluster-resident, %d CTAs per solve" % tuning[0]) if tuning[0]
-           else "streaming, %d rows/thread, %d warps/block" % (tuning[1], tuning[2]),
+           "stencil_kernel": kernel_label(tuning),
            "clocks": clk.summary()}
     if args.workload == "layered":
         out["eig"] = float(eig.item())
@@ -540,8 +555,7 @@ def run_paper_scenarios(args, rank, world, local):
     rules["monte_carlo_10000"] = (lo + (hi - lo) * u, np.full(10000, 1e-4))
     out = {"metric": "paper model problem, Scenarios I-III (Sec. 4.5)", "workload": w.name,
            "jacobian": "sensitivity (Alg. 1 steps 1-5)", "sigma": sigma,
-           "stencil_kernel": ("cluster-resident, %d CTAs per solve" % tuning[0]) if tuning[0]
-           else "streaming", "rules": {}}
+           "stencil_kernel": kernel_label(tuning), "rules": {}}
     for name, (x, wt) in rules.items():
         n = x.shape[0]
         th = torch.tensor(x, device=dev)

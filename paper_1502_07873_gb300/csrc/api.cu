@@ -90,6 +90,7 @@ static Sizes sizes(const Geometry &g, int precision, int max_solves)
     s.trace = al((size_t)max_solves * g.nlev * g.nrec * 2 * e);
     s.theta = al((size_t)max_solves * kNT * sizeof(double));
     s.rows = al((size_t)g.nz * (precision == OED_FP64 ? sizeof(RowCoef<double>) : sizeof(RowCoef<float>)));
+    s.rows += al((size_t)g.nz * (precision == OED_FP64 ? sizeof(FacCoef<double>) : sizeof(FacCoef<float>)));
     s.rec = al((size_t)g.nrec * sizeof(int));
     s.hseg = al((size_t)chunk * 16 * g.nrec * 28 * sizeof(double));
     s.err = 256;
@@ -218,7 +219,11 @@ int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
     ctx->d_stf = q; q += s.stf;
     ctx->d_trace = q; q += s.trace;
     ctx->d_theta = (double *)q; q += s.theta;
-    ctx->d_rows = q; q += s.rows;
+    ctx->d_rows = q;
+    ctx->d_fac = q + ((size_t)ctx->g.nz * (ctx->precision == OED_FP64 ? sizeof(RowCoef<double>)
+                                                                       : sizeof(RowCoef<float>)) +
+                      255) / 256 * 256;
+    q += s.rows;
     ctx->d_rec = (int *)q; q += s.rec;
     ctx->d_hseg = (double *)q; q += s.hseg;
     ctx->d_err = (int *)q; q += s.err;

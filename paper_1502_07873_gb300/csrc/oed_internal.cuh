@@ -44,6 +44,25 @@ struct __align__(16 * sizeof(real)) RowCoef {
     real axx, azx, axzp, axzm, azzp, azzm, lx, mxp, mxm, mz, lzp, lzm, rf, cp, cs, pad;
 };
 
+// The same update regrouped so that FP32 rounds as little as possible at the
+// scale of u itself: every neighbour enters through a difference, the operator
+// term is summed at the (small) scale of those differences, and u^{m+1} is formed
+// as u^m + ((u^m - u^{m-1}) + A), one rounding at the scale of u per step.
+//   A_x = axx lap_x + axzp dv_s + naxzm dv_n + px dz_s + nqx dz_n
+//   A_z = azx lap_z + azzp dw_s + nazzm dw_n + pz dx_s + nqz dx_n
+// with lap_x = (x_e - x_c) - (x_c - x_w), dv_s = x_s - x_c, dv_n = x_c - x_n (dw for
+// u_z likewise), dz_r = z_re - z_rw and dx_r = x_re - x_rw on row r, and
+//   naxzm = -axzm, px = lx + mxp, nqx = -(lx + mxm),
+//   nazzm = -azzm, pz = mz + lzp, nqz = -(mz + lzm)
+// on interior rows.  On the surface row the north terms vanish (naxzm = nazzm = 0)
+// and the cross terms use the row itself: dz_n -> dz_c, dx_n -> dx_c, with
+// nqx = mxm - lx, nqz = lzm - mz.  cp, cs as in RowCoef.  Built from the FP64
+// coefficients by the same kernel.
+template <typename real>
+struct __align__(16 * sizeof(real)) FacCoef {
+    real axx, axzp, naxzm, px, nqx, azx, azzp, nazzm, pz, nqz, cp, cs, pad0, pad1, pad2, pad3;
+};
+
 // Source of one solve: corner of the 7x7 patch and the spatial force density
 // f_x, f_z (Eq. source with the regularised delta / delta' of Sec. 3.3.2),
 // already multiplied by dt^2/nu of the patch rows.  The forcing at step m is
@@ -84,6 +103,7 @@ struct oed_ctx {
     std::vector<int> rec_ix;
     // device workspace
     void *d_rows = nullptr;    // RowCoef<real>[nz]
+    void *d_fac = nullptr;     // FacCoef<real>[nz] (same rows, factored form)
     int *d_rec = nullptr;      // [nrec]
     int *d_err = nullptr;      // device flag: a bounded wait in a kernel expired
     void *d_u0 = nullptr;      // wavefield level buffer A [max_solves][2][nz][xp]

@@ -228,7 +228,7 @@ __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, in
 // Per-row coefficients (one thread per row).
 template <typename real>
 __global__ void k_rows(Geometry g, int nlayers, const double *__restrict__ lay,
-                       RowCoef<real> *__restrict__ rows)
+                       RowCoef<real> *__restrict__ rows, FacCoef<real> *__restrict__ fac)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= g.nz) return;
@@ -293,6 +293,19 @@ __global__ void k_rows(Geometry g, int nlayers, const double *__restrict__ lay,
     o.mxm = (real)c.mxm; o.mz = (real)c.mz; o.lzp = (real)c.lzp; o.lzm = (real)c.lzm;
     o.rf = (real)c.rf; o.cp = (real)c.cp; o.cs = (real)c.cs; o.pad = (real)0;
     rows[j] = o;
+    FacCoef<double> f;
+    f.axx = c.axx; f.axzp = c.axzp; f.naxzm = -c.axzm;
+    f.azx = c.azx; f.azzp = c.azzp; f.nazzm = -c.azzm;
+    f.px = c.lx + c.mxp;
+    f.pz = c.mz + c.lzp;
+    f.nqx = j == 0 ? c.mxm - c.lx : -(c.lx + c.mxm);
+    f.nqz = j == 0 ? c.lzm - c.mz : -(c.mz + c.lzm);
+    FacCoef<real> q;
+    q.axx = (real)f.axx; q.axzp = (real)f.axzp; q.naxzm = (real)f.naxzm; q.px = (real)f.px;
+    q.nqx = (real)f.nqx; q.azx = (real)f.azx; q.azzp = (real)f.azzp; q.nazzm = (real)f.nazzm;
+    q.pz = (real)f.pz; q.nqz = (real)f.nqz; q.cp = (real)c.cp; q.cs = (real)c.cs;
+    q.pad0 = q.pad1 = q.pad2 = q.pad3 = (real)0;
+    fac[j] = q;
 }
 
 void launch_rows(oed_ctx *ctx, cudaStream_t s)
@@ -310,9 +323,11 @@ void launch_rows(oed_ctx *ctx, cudaStream_t s)
     cudaMemcpyAsync(d_lay, lay.data(), sizeof(double) * lay.size(), cudaMemcpyHostToDevice, s);
     const int nb = (ctx->g.nz + 127) / 128;
     if (ctx->precision == OED_FP64)
-        k_rows<double><<<nb, 128, 0, s>>>(ctx->g, nl, d_lay, (RowCoef<double> *)ctx->d_rows);
+        k_rows<double><<<nb, 128, 0, s>>>(ctx->g, nl, d_lay, (RowCoef<double> *)ctx->d_rows,
+                                           (FacCoef<double> *)ctx->d_fac);
     else
-        k_rows<float><<<nb, 128, 0, s>>>(ctx->g, nl, d_lay, (RowCoef<float> *)ctx->d_rows);
+        k_rows<float><<<nb, 128, 0, s>>>(ctx->g, nl, d_lay, (RowCoef<float> *)ctx->d_rows,
+                                          (FacCoef<float> *)ctx->d_fac);
     cudaFreeAsync(d_lay, s);
     cudaStreamSynchronize(s);   // the host vector `lay` must outlive the copy
 }

@@ -29,7 +29,7 @@ template <typename real>
 struct StepArgs {
     const real *cur;               // u^m
     real *nxt;                     // u^{m-1} in, u^{m+1} out
-    const RowCoef<real> *rows;     // [nz]
+    const FacCoef<real> *fac;      // [nz]
     const SourceDesc<real> *src;   // [nsolve]
     const real *stf;               // [nsolve][nsteps]
     real *trace;                   // [nsolve][nlev][nrec][2]
@@ -102,16 +102,15 @@ __global__ void __launch_bounds__(256) k_step(StepArgs<real> a)
     for (int k = 0; k < ZS; k++) {
         const int j = jb + k;
         if (j > jlast) break;
-        const RowCoef<real> R = a.rows[j];
-        const int b = j - sj;
-        real fx = (real)0, fz = (real)0;
-        if (scol && (unsigned)b < (unsigned)kPatch) {
-            fx = S * a.src[s].wx[b * kPatch + si];
-            fz = S * a.src[s].wz[b * kPatch + si];
-        }
+        const FacCoef<real> K = a.fac[j];
         real ux, uz;
-        cell_update(R, X[k], X[k + 1], X[k + 2], Z[k], Z[k + 1], Z[k + 2], XM[k], ZM[k], side,
-                    j == jlast, j == 0, fx, fz, ux, uz);
+        node_update(K, X[k], X[k + 1], X[k + 2], Z[k], Z[k + 1], Z[k + 2], XM[k], ZM[k], side,
+                    j == jlast, j == 0, ux, uz);
+        const int b = j - sj;
+        if (scol && (unsigned)b < (unsigned)kPatch && !side && j != jlast) {
+            ux = add_force(ux, S, a.src[s].wx[b * kPatch + si]);
+            uz = add_force(uz, S, a.src[s].wz[b * kPatch + si]);
+        }
         const size_t o = (size_t)j * g.xp + i;
         __stcs(px + o, ux);   // u^{m+1} is next read one full step later: streaming
         __stcs(pz + o, uz);
@@ -143,7 +142,7 @@ static void launch_steps_zs(const oed_ctx *ctx, int nsolve, cudaStream_t st, cud
     dim3 grid((g.nx + 31) / 32, (g.nz + rows_per_block - 1) / rows_per_block, nsolve);
     real *u0 = (real *)ctx->d_u0, *u1 = (real *)ctx->d_u1;
     StepArgs<real> a;
-    a.rows = (const RowCoef<real> *)ctx->d_rows;
+    a.fac = (const FacCoef<real> *)ctx->d_fac;
     a.src = (const SourceDesc<real> *)ctx->d_src;
     a.stf = (const real *)ctx->d_stf;
     a.trace = (real *)ctx->d_trace;
@@ -186,7 +185,7 @@ static void probe_zs(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st, 
     const int rows_per_block = wz * ZS;
     dim3 grid((g.nx + 31) / 32, (g.nz + rows_per_block - 1) / rows_per_block, nsolve);
     StepArgs<real> a;
-    a.rows = (const RowCoef<real> *)ctx->d_rows;
+    a.fac = (const FacCoef<real> *)ctx->d_fac;
     a.src = (const SourceDesc<real> *)ctx->d_src;
     a.stf = (const real *)ctx->d_stf;
     a.trace = (real *)ctx->d_trace;

@@ -38,7 +38,7 @@ constexpr int kSmemBytes = kStages * kStageBytes + 128 /* alignment slack */ + 1
 
 struct TmaArgs {
     float *nxt;                   // u^{m-1} in, u^{m+1} out (global)
-    const RowCoef<float> *rows;
+    const FacCoef<float> *fac;
     const SourceDesc<float> *src;
     const float *stf;
     float *trace;
@@ -214,16 +214,15 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
                     Z[2][c] = hz[(r + 2) * kWX + cx + kHX - 1 + c];
                 }
                 if (z < g.nz) {
-                    const RowCoef<float> R = a.rows[z];
-                    float fx = 0.0f, fz = 0.0f;
-                    const int b = z - sd->j0;
-                    if (scol && (unsigned)b < (unsigned)kPatch) {
-                        fx = S * sd->wx[b * kPatch + si];
-                        fz = S * sd->wz[b * kPatch + si];
-                    }
+                    const FacCoef<float> K = a.fac[z];
                     float ux, uz;
-                    cell_update(R, W[0], W[1], W[2], Z[0], Z[1], Z[2], px[r * kTX + cx], pz[r * kTX + cx],
-                                side, z == g.nz - 1, z == 0, fx, fz, ux, uz);
+                    node_update(K, W[0], W[1], W[2], Z[0], Z[1], Z[2], px[r * kTX + cx], pz[r * kTX + cx],
+                                side, z == g.nz - 1, z == 0, ux, uz);
+                    const int b = z - sd->j0;
+                    if (scol && (unsigned)b < (unsigned)kPatch && !side && z != g.nz - 1) {
+                        ux = add_force(ux, S, sd->wx[b * kPatch + si]);
+                        uz = add_force(uz, S, sd->wz[b * kPatch + si]);
+                    }
                     const size_t o = (size_t)z * g.xp + x;
                     __stcs(gx + o, ux);
                     __stcs(gz + o, uz);
@@ -304,7 +303,7 @@ cudaError_t launch_steps_tma(const oed_ctx *ctx, int nsolve, cudaStream_t st, cu
     const int smem = kSmemBytes;
     if (ctx->tma_ctas < 1) return cudaErrorInvalidConfiguration;
     TmaArgs a;
-    a.rows = (const RowCoef<float> *)ctx->d_rows;
+    a.fac = (const FacCoef<float> *)ctx->d_fac;
     a.src = (const SourceDesc<float> *)ctx->d_src;
     a.stf = (const float *)ctx->d_stf;
     a.trace = (float *)ctx->d_trace;
