@@ -1,34 +1,35 @@
 // Cluster-resident time stepping: one thread-block cluster integrates one solve
 // through all of its time steps with the wavefield held in distributed shared
-// memory (Sec. 3.3.1, Eq. Full_Disc, in the factored form of FacCoef).
+// memory (Sec. 3.3.1, Eq. Full_Disc; the node update of stencil_cell.cuh).
 //
 // CTA r of a cluster of C owns rows [r R, min((r+1) R, nz)) of the grid, both
 // components and both time levels, in its shared memory:
-//     A_x, A_z, B_x, B_z : [R][sxp] floats,   coef : [R] FacCoef
-// Column i of a row sits at offset i + kGhost; the columns -1, nx and nx + 1 are
-// zero ghosts, so every thread reads its west and east neighbours at fixed
-// offsets.  Level m lives in A (m even) or B (m odd); u^{m+1} overwrites u^{m-1}
-// in place.  The rows just above and below a CTA's slab are read straight from the
-// neighbouring CTA's shared memory (mapa + ld.shared::cluster).  One cluster
-// barrier (arrive.release / wait.acquire) per step orders the writes of step m
-// before the reads of step m+1 and the reads of step m before the overwrites of
-// step m+1.  Every thread of every CTA executes the same number of barriers.
-// Each thread owns a pair of adjacent columns (64-bit shared loads and stores)
-// and marches down a segment of the slab's rows.  A row enters the register
-// window once, as the south row, where its centre values, west + east sums and
-// east - west differences are formed; they serve it again as the centre row and
-// as the north row, so a node costs six multiply-adds per component.  The
-// surface row, the bottom row and the rows whose neighbour lives in another CTA
-// are peeled off the main loop; the absorbing side columns are patched by the
+//     A, B : [R][npair + 2] float4,   coef : [R] FacCoef
+// Slot q of a row holds the column pair p = q - 1 as (x_2p, z_2p, x_2p+1, z_2p+1);
+// slots 0 and npair + 1 (columns -2, -1, nx.., and column nx when nx is odd) are
+// zero ghosts, so a thread owning pair p reads its whole neighbourhood with one
+// 128-bit load (its pair) and two 64-bit loads (the west column of slot p and the
+// east column of slot p + 2), both components at once.  Level m lives in A (m
+// even) or B (m odd); u^{m+1} overwrites u^{m-1} in place.  The rows just above
+// and below a CTA's slab are read straight from the neighbouring CTA's shared
+// memory (mapa + ld.shared::cluster).  One cluster barrier (arrive.release /
+// wait.acquire) per step orders the writes of step m before the reads of step
+// m+1 and the reads of step m before the overwrites of step m+1; every thread of
+// every CTA executes the same number of barriers.  Threads are packed densely
+// over (row segment, column pair); each marches down its segment.  A row enters
+// the register window once, as the south row, where its second differences and
+// east - west differences are formed; its south differences are formed when the
+// next row arrives, and all of them serve it again as the centre and north row.
+// The surface row, the bottom row and the rows whose neighbour lives in another
+// CTA are peeled off the main loop; the absorbing side columns are patched by the
 // threads that own them; the source term is added after the sweep to the few
 // patch nodes.  HBM traffic is only the seismogram samples and the source time
 // function: the wavefield never leaves the chip, so this kernel is bound by
-// instruction issue and shared-memory traffic, not by HBM.
+// instruction issue, shared-memory latency and the per-step barrier, not by HBM.
 #include "stencil_cell.cuh"
 
 namespace oed {
 
-constexpr int kGhost = 2;   // offset of column 0 in a shared row (keeps pairs 8-byte aligned)
 // Block size and register budget: registers are split over the SM's four
 // schedulers (16 K each), so 20 warps of 96 registers is the most one CTA can hold
 // with the row window in registers.
@@ -43,7 +44,7 @@ struct ResArgs {
     const int *rec;                // [nrec]
     Geometry g;
     int R;                         // rows per CTA
-    int sxp;                       // shared row stride (floats)
+    int sq;                        // float4 slots per shared row, npair + 2
     int npair;                     // column pairs per row, (nx + 1) / 2
     int nseg;                      // row segments per column pair
     int rps;                       // rows per segment
@@ -75,10 +76,20 @@ __device__ __forceinline__ unsigned remote_addr(unsigned local, unsigned rank)
     return r;
 }
 
-__device__ __forceinline__ float ld_cluster(unsigned addr)
+__device__ __forceinline__ float4 ld_cluster4(unsigned addr)
 {
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float2 ld_cluster2(unsigned addr)
+{
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
     return v;
 }
 
@@ -93,34 +104,36 @@ struct Row2 {
     float vxa, vxb, vza, vzb;
 };
 
-__device__ __forceinline__ void row_from(float w, float2 m, float e, float &va, float &vb, float &la,
-                                         float &lb, float &da, float &db)
+// w = (x, z) of the west column, m = the pair, e = (x, z) of the east column
+__device__ __forceinline__ void row_from(float2 w, float4 m, float2 e, Row2 &r)
 {
-    va = m.x;
-    vb = m.y;
-    la = (m.y - m.x) - (m.x - w);
-    lb = (e - m.y) - (m.y - m.x);
-    da = m.y - w;
-    db = e - m.x;
+    r.xa = m.x;
+    r.za = m.y;
+    r.xb = m.z;
+    r.zb = m.w;
+    r.lxa = (m.z - m.x) - (m.x - w.x);
+    r.lxb = (e.x - m.z) - (m.z - m.x);
+    r.lza = (m.w - m.y) - (m.y - w.y);
+    r.lzb = (e.y - m.w) - (m.w - m.y);
+    r.dxa = m.z - w.x;
+    r.dxb = e.x - m.x;
+    r.dza = m.w - w.y;
+    r.dzb = e.y - m.y;
 }
 
-// px, pz point at column c of a local row of each component
-__device__ __forceinline__ void load_row(const float *px, const float *pz, Row2 &r)
+// q points at the thread's own slot of a local row
+__device__ __forceinline__ void load_row(const float4 *q, Row2 &r)
 {
-    const float2 mx = *reinterpret_cast<const float2 *>(px);
-    const float2 mz = *reinterpret_cast<const float2 *>(pz);
-    row_from(px[-1], mx, px[2], r.xa, r.xb, r.lxa, r.lxb, r.dxa, r.dxb);
-    row_from(pz[-1], mz, pz[2], r.za, r.zb, r.lza, r.lzb, r.dza, r.dzb);
+    const float2 w = *reinterpret_cast<const float2 *>(&q[-1].z);
+    const float2 e = *reinterpret_cast<const float2 *>(&q[1].x);
+    row_from(w, *q, e, r);
 }
 
-// the same row in CTA `nb` of the cluster (local pointers are mapped)
-__device__ __forceinline__ void load_row_remote(const float *px, const float *pz, unsigned nb, Row2 &r)
+// the same slot of a row in CTA `nb` of the cluster
+__device__ __forceinline__ void load_row_remote(const float4 *q, unsigned nb, Row2 &r)
 {
-    const unsigned bx = remote_addr(smem_addr(px), nb), bz = remote_addr(smem_addr(pz), nb);
-    const float2 mx = make_float2(ld_cluster(bx), ld_cluster(bx + 4u));
-    const float2 mz = make_float2(ld_cluster(bz), ld_cluster(bz + 4u));
-    row_from(ld_cluster(bx - 4u), mx, ld_cluster(bx + 8u), r.xa, r.xb, r.lxa, r.lxb, r.dxa, r.dxb);
-    row_from(ld_cluster(bz - 4u), mz, ld_cluster(bz + 8u), r.za, r.zb, r.lza, r.lzb, r.dza, r.dzb);
+    const unsigned b = remote_addr(smem_addr(q), nb);
+    row_from(ld_cluster2(b - 8u), ld_cluster4(b), ld_cluster2(b + 16u), r);
 }
 
 // south differences of row c once its south row s is loaded
@@ -134,14 +147,14 @@ __device__ __forceinline__ void south(Row2 &c, const Row2 &s)
 
 // u^{m+1} of the pair from the rows n, c, s (the node update of stencil_cell.cuh);
 // n supplies the north differences (its south ones) and the north cross terms.
-// ux, uz hold u^{m-1} on entry.
+// u holds u^{m-1} on entry, in slot order (x_a, z_a, x_b, z_b).
 __device__ __forceinline__ void pair_update(const FacCoef<float> &K, const Row2 &n, const Row2 &c,
-                                            const Row2 &s, float2 &ux, float2 &uz)
+                                            const Row2 &s, float4 &u)
 {
-    ux.x = leap(c.xa, ux.x, op_x(K, c.lxa, c.vxa, n.vxa, s.dza, n.dza));
-    ux.y = leap(c.xb, ux.y, op_x(K, c.lxb, c.vxb, n.vxb, s.dzb, n.dzb));
-    uz.x = leap(c.za, uz.x, op_z(K, c.lza, c.vza, n.vza, s.dxa, n.dxa));
-    uz.y = leap(c.zb, uz.y, op_z(K, c.lzb, c.vzb, n.vzb, s.dxb, n.dxb));
+    u.x = leap(c.xa, u.x, op_x(K, c.lxa, c.vxa, n.vxa, s.dza, n.dza));
+    u.z = leap(c.xb, u.z, op_x(K, c.lxb, c.vxb, n.vxb, s.dzb, n.dzb));
+    u.y = leap(c.za, u.y, op_z(K, c.lza, c.vza, n.vza, s.dxa, n.dxa));
+    u.w = leap(c.zb, u.w, op_z(K, c.lzb, c.vzb, n.vzb, s.dxb, n.dxb));
 }
 
 // Absorbing rows: the bottom row from its north neighbour, then the side columns
@@ -149,57 +162,57 @@ __device__ __forceinline__ void pair_update(const FacCoef<float> &K, const Row2 
 // bit 0 node c is column 0, bit 1 node c+1 is column nx-1, bit 2 node c is column
 // nx-1 (node c+1 is then the ghost and stays zero).
 __device__ __forceinline__ void absorbing(float cp, float cs, const Row2 &n, const Row2 &c, bool bottom,
-                                          int kind, float2 &ux, float2 &uz)
+                                          int kind, float4 &u)
 {
     if (bottom) {
-        ux.x = absorb(c.xa, n.xa, cs);
-        ux.y = absorb(c.xb, n.xb, cs);
-        uz.x = absorb(c.za, n.za, cp);
-        uz.y = absorb(c.zb, n.zb, cp);
+        u.x = absorb(c.xa, n.xa, cs);
+        u.z = absorb(c.xb, n.xb, cs);
+        u.y = absorb(c.za, n.za, cp);
+        u.w = absorb(c.zb, n.zb, cp);
     }
     if (kind & 1) {
-        ux.x = absorb(c.xa, c.xb, cp);
-        uz.x = absorb(c.za, c.zb, cs);
+        u.x = absorb(c.xa, c.xb, cp);
+        u.y = absorb(c.za, c.zb, cs);
     }
     if (kind & 2) {
-        ux.y = absorb(c.xb, c.xa, cp);
-        uz.y = absorb(c.zb, c.za, cs);
+        u.z = absorb(c.xb, c.xa, cp);
+        u.w = absorb(c.zb, c.za, cs);
     }
     if (kind & 4) {   // column nx-1: its east - west difference is -west (the ghost east is 0)
-        ux.x = absorb(c.xa, -c.dxa, cp);
-        uz.x = absorb(c.za, -c.dza, cs);
-        ux.y = 0.0f;
-        uz.y = 0.0f;
+        u.x = absorb(c.xa, -c.dxa, cp);
+        u.y = absorb(c.za, -c.dza, cs);
+        u.z = 0.0f;
+        u.w = 0.0f;
     }
+}
+
+// float offset of node (column i, component comp) within a shared row
+__device__ __forceinline__ int node_off(int i, int comp)
+{
+    return ((i >> 1) + 1) * 4 + (i & 1) * 2 + comp;
 }
 
 __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
 {
     extern __shared__ float4 smem4[];
-    float *sm = reinterpret_cast<float *>(smem4);
     const Geometry &g = a.g;
     const unsigned rank = cluster_rank();
     const int s = blockIdx.y;
-    const int R = a.R, sxp = a.sxp;
+    const int R = a.R, sq = a.sq;
     const int j0 = (int)rank * R;
     const int nrows = max(0, min(R, g.nz - j0));
-    const int lvl = R * sxp;   // floats per component and level
-    float *Ax = sm, *Az = sm + lvl, *Bx = sm + 2 * lvl, *Bz = sm + 3 * lvl;
-    FacCoef<float> *coef = reinterpret_cast<FacCoef<float> *>(sm + 4 * lvl);
+    const int lvl = R * sq;   // float4 slots per level
+    float4 *A = smem4, *B = smem4 + lvl;
+    FacCoef<float> *coef = reinterpret_cast<FacCoef<float> *>(smem4 + 2 * lvl);
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
 
-    for (int k = tid; k < lvl; k += nthr) {   // u^0 = u^{-1} = 0, ghosts 0
-        Ax[k] = 0.0f;
-        Az[k] = 0.0f;
-        Bx[k] = 0.0f;
-        Bz[k] = 0.0f;
-    }
+    for (int k = tid; k < 2 * lvl; k += nthr) smem4[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int k = tid; k < nrows; k += nthr) coef[k] = a.fac[j0 + k];
 
-    // thread -> column pair (c, c+1) and row segment [l0, l1) of the slab
     // threads are packed densely over (segment, pair): a warp may straddle two segments
-    const int c = 2 * (tid % a.npair);
+    const int p = tid % a.npair;
+    const int c = 2 * p;
     const int seg = tid / a.npair;
     const bool active = seg < a.nseg;
     const int kind = (c == 0 ? 1 : 0) | (c + 1 == g.nx - 1 ? 2 : 0) | (c == g.nx - 1 ? 4 : 0);
@@ -213,65 +226,61 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     const bool scolB = c + 1 < g.nx && (unsigned)siB < (unsigned)kPatch;
     const float *stf = a.stf + (size_t)s * g.nsteps;
     float *trace = a.trace + (size_t)s * g.nlev * g.nrec * 2;
-    const int col = c + kGhost;
     cluster_barrier();
 
     for (int m = 0; m < g.nsteps; m++) {
-        const float *cx = (m & 1) ? Bx : Ax, *cz = (m & 1) ? Bz : Az;
-        float *nxb = (m & 1) ? Ax : Bx, *nzb = (m & 1) ? Az : Bz;
-        if (rank == 0)
+        const float4 *cur = ((m & 1) ? B : A) + p + 1;   // this thread's slot in row 0
+        float4 *nxt = ((m & 1) ? A : B) + p + 1;
+        if (rank == 0) {
+            const float *row0 = reinterpret_cast<const float *>((m & 1) ? B : A);
             for (int q = tid; q < 2 * g.nrec; q += nthr)
-                trace[(size_t)m * g.nrec * 2 + q] = (q & 1 ? cz : cx)[a.rec[q >> 1] + kGhost];
+                trace[(size_t)m * g.nrec * 2 + q] = row0[node_off(a.rec[q >> 1], q & 1)];
+        }
         if (active && l0 < l1) {
             Row2 rn, rc, rs;
             int l = l0;
-            load_row(cx + l * sxp + col, cz + l * sxp + col, rc);
-            if (top) {   // surface row: its "north" terms are the row itself
+            load_row(cur + l * sq, rc);
+            if (top) {   // surface row: no north differences, cross terms on the row itself
                 if (l + 1 < nrows)
-                    load_row(cx + (l + 1) * sxp + col, cz + (l + 1) * sxp + col, rs);
+                    load_row(cur + (l + 1) * sq, rs);
                 else   // a one-row slab
-                    load_row_remote(cx + col, cz + col, rank + 1, rs);
+                    load_row_remote(cur, rank + 1, rs);
                 south(rc, rs);
-                Row2 nt = rc;   // no north differences; cross terms on the row itself
+                Row2 nt = rc;
                 nt.vxa = nt.vxb = nt.vza = nt.vzb = 0.0f;
-                float2 *px = reinterpret_cast<float2 *>(nxb + l * sxp + col);
-                float2 *pz = reinterpret_cast<float2 *>(nzb + l * sxp + col);
-                float2 ux = *px, uz = *pz;
+                float4 *o = nxt + l * sq;
+                float4 u = *o;
                 const FacCoef<float> K = coef[l];
-                pair_update(K, nt, rc, rs, ux, uz);
-                if (kind) absorbing(K.cp, K.cs, nt, rc, false, kind, ux, uz);
-                *px = ux;
-                *pz = uz;
+                pair_update(K, nt, rc, rs, u);
+                if (kind) absorbing(K.cp, K.cs, nt, rc, false, kind, u);
+                *o = u;
                 rn = rc;
                 rc = rs;
                 l++;
             } else {
                 if (l > 0)
-                    load_row(cx + (l - 1) * sxp + col, cz + (l - 1) * sxp + col, rn);
+                    load_row(cur + (l - 1) * sq, rn);
                 else
-                    load_row_remote(cx + (R - 1) * sxp + col, cz + (R - 1) * sxp + col, rank - 1, rn);
+                    load_row_remote(cur + (R - 1) * sq, rank - 1, rn);
                 south(rn, rc);
             }
             // rows whose south neighbour is a local row and that are not the bottom row:
             // unrolled by three with the three window rows taking turns
             const int lstop = min(l1, nrows - 1);
             {
-                const float *sx = cx + (l + 1) * sxp + col, *sz = cz + (l + 1) * sxp + col;
-                float *ox = nxb + l * sxp + col, *oz = nzb + l * sxp + col;
+                const float4 *sp = cur + (l + 1) * sq;
+                float4 *o = nxt + l * sq;
                 const FacCoef<float> *cf = coef + l;
                 auto row = [&](const Row2 &wn, Row2 &wc, Row2 &ws) {
-                    load_row(sx, sz, ws);
+                    load_row(sp, ws);
                     south(wc, ws);
                     const FacCoef<float> K = *cf;
-                    float2 ux = *reinterpret_cast<float2 *>(ox), uz = *reinterpret_cast<float2 *>(oz);
-                    pair_update(K, wn, wc, ws, ux, uz);
-                    if (kind) absorbing(K.cp, K.cs, wn, wc, false, kind, ux, uz);
-                    *reinterpret_cast<float2 *>(ox) = ux;
-                    *reinterpret_cast<float2 *>(oz) = uz;
-                    sx += sxp;
-                    sz += sxp;
-                    ox += sxp;
-                    oz += sxp;
+                    float4 u = *o;
+                    pair_update(K, wn, wc, ws, u);
+                    if (kind) absorbing(K.cp, K.cs, wn, wc, false, kind, u);
+                    *o = u;
+                    sp += sq;
+                    o += sq;
                     cf++;
                 };
                 for (; l + 3 <= lstop; l += 3) {
@@ -289,19 +298,17 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
             // or the absorbing bottom row
             for (; l < l1; l++) {
                 const FacCoef<float> K = coef[l];
-                float2 *px = reinterpret_cast<float2 *>(nxb + l * sxp + col);
-                float2 *pz = reinterpret_cast<float2 *>(nzb + l * sxp + col);
-                float2 ux = *px, uz = *pz;
+                float4 *o = nxt + l * sq;
+                float4 u = *o;
                 if (j0 + l == g.nz - 1) {
-                    absorbing(K.cp, K.cs, rn, rc, true, kind, ux, uz);
+                    absorbing(K.cp, K.cs, rn, rc, true, kind, u);
                 } else {
-                    load_row_remote(cx + col, cz + col, rank + 1, rs);
+                    load_row_remote(cur, rank + 1, rs);
                     south(rc, rs);
-                    pair_update(K, rn, rc, rs, ux, uz);
-                    if (kind) absorbing(K.cp, K.cs, rn, rc, false, kind, ux, uz);
+                    pair_update(K, rn, rc, rs, u);
+                    if (kind) absorbing(K.cp, K.cs, rn, rc, false, kind, u);
                 }
-                *px = ux;
-                *pz = uz;
+                *o = u;
                 rn = rc;
                 rc = rs;
             }
@@ -309,17 +316,20 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
             // added last as in the node update of the streaming kernel
             if (scolA || scolB) {
                 const float S = stf[m];
+                float *nf = reinterpret_cast<float *>((m & 1) ? A : B);
                 for (int bb = 0; bb < kPatch; bb++) {
                     const int lj = sj + bb - j0;
                     if (lj < l0 || lj >= l1) continue;
-                    const int o = lj * sxp + col;
+                    float *row = nf + (size_t)lj * sq * 4;
                     if (scolA) {
-                        nxb[o] = add_force(nxb[o], S, sd->wx[bb * kPatch + siA]);
-                        nzb[o] = add_force(nzb[o], S, sd->wz[bb * kPatch + siA]);
+                        row[node_off(c, 0)] = add_force(row[node_off(c, 0)], S, sd->wx[bb * kPatch + siA]);
+                        row[node_off(c, 1)] = add_force(row[node_off(c, 1)], S, sd->wz[bb * kPatch + siA]);
                     }
                     if (scolB) {
-                        nxb[o + 1] = add_force(nxb[o + 1], S, sd->wx[bb * kPatch + siB]);
-                        nzb[o + 1] = add_force(nzb[o + 1], S, sd->wz[bb * kPatch + siB]);
+                        row[node_off(c + 1, 0)] =
+                            add_force(row[node_off(c + 1, 0)], S, sd->wx[bb * kPatch + siB]);
+                        row[node_off(c + 1, 1)] =
+                            add_force(row[node_off(c + 1, 1)], S, sd->wz[bb * kPatch + siB]);
                     }
                 }
             }
@@ -327,16 +337,16 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
         cluster_barrier();
     }
     if (rank == 0) {
-        const float *cx = (g.nsteps & 1) ? Bx : Ax, *cz = (g.nsteps & 1) ? Bz : Az;
+        const float *row0 = reinterpret_cast<const float *>((g.nsteps & 1) ? B : A);
         for (int q = tid; q < 2 * g.nrec; q += nthr)
-            trace[(size_t)g.nsteps * g.nrec * 2 + q] = (q & 1 ? cz : cx)[a.rec[q >> 1] + kGhost];
+            trace[(size_t)g.nsteps * g.nrec * 2 + q] = row0[node_off(a.rec[q >> 1], q & 1)];
     }
 }
 
 // Shape of the resident launch for a grid: cluster size C (1..8) and rows per CTA,
 // or C = 0 when the two levels do not fit in C CTAs of shared memory.
 struct ResShape {
-    int C, R, sxp, npair, nseg, rps, threads;
+    int C, R, sq, npair, nseg, rps, threads;
     size_t smem;
 };
 
@@ -347,14 +357,14 @@ static ResShape resident_shape(const Geometry &g, int C)
     if (npair > kResThreads || C < 1 || C > 8) return r;
     const int R = (g.nz + C - 1) / C;
     if ((C - 1) * R >= g.nz) return r;   // a CTA would own no rows
-    const int sxp = (g.nx + kGhost + 2 + 3) / 4 * 4;   // ghosts at -1, nx, nx + 1
-    const size_t smem = (size_t)4 * R * sxp * sizeof(float) + (size_t)R * sizeof(FacCoef<float>);
+    const int sq = npair + 2;   // ghost slots on both sides
+    const size_t smem = (size_t)2 * R * sq * sizeof(float4) + (size_t)R * sizeof(FacCoef<float>);
     if (smem > 227 * 1024) return r;
     int nseg = kResThreads / npair;
     if (nseg > R) nseg = R;
     r.C = C;
     r.R = R;
-    r.sxp = sxp;
+    r.sq = sq;
     r.npair = npair;
     r.nseg = nseg;
     r.rps = (R + nseg - 1) / nseg;
@@ -423,7 +433,7 @@ cudaError_t launch_resident(const oed_ctx *ctx, int C, int nsolve, cudaStream_t 
     a.g = ctx->g;
     if (nsteps_override > 0 && nsteps_override < a.g.nsteps) a.g.nsteps = nsteps_override;
     a.R = r.R;
-    a.sxp = r.sxp;
+    a.sq = r.sq;
     a.npair = r.npair;
     a.nseg = r.nseg;
     a.rps = r.rps;
