@@ -161,14 +161,15 @@ __device__ __forceinline__ void pair_update(const FacCoef<float> &K, const Row2 
 // (which take precedence at the corners) from their interior neighbour.  kind:
 // bit 0 node c is column 0, bit 1 node c+1 is column nx-1, bit 2 node c is column
 // nx-1 (node c+1 is then the ghost and stays zero).
-__device__ __forceinline__ void absorbing(float cp, float cs, const Row2 &n, const Row2 &c, bool bottom,
+// (nv: the north row's slot, used by the bottom row only)
+__device__ __forceinline__ void absorbing(float cp, float cs, float4 nv, const Row2 &c, bool bottom,
                                           int kind, float4 &u)
 {
     if (bottom) {
-        u.x = absorb(c.xa, n.xa, cs);
-        u.z = absorb(c.xb, n.xb, cs);
-        u.y = absorb(c.za, n.za, cp);
-        u.w = absorb(c.zb, n.zb, cp);
+        u.x = absorb(c.xa, nv.x, cs);
+        u.z = absorb(c.xb, nv.z, cs);
+        u.y = absorb(c.za, nv.y, cp);
+        u.w = absorb(c.zb, nv.w, cp);
     }
     if (kind & 1) {
         u.x = absorb(c.xa, c.xb, cp);
@@ -252,7 +253,7 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 float4 u = *o;
                 const FacCoef<float> K = coef[l];
                 pair_update(K, nt, rc, rs, u);
-                if (kind) absorbing(K.cp, K.cs, nt, rc, false, kind, u);
+                if (kind) absorbing(K.cp, K.cs, u, rc, false, kind, u);
                 *o = u;
                 rn = rc;
                 rc = rs;
@@ -267,19 +268,30 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
             // rows whose south neighbour is a local row and that are not the bottom row:
             // unrolled by three with the three window rows taking turns
             const int lstop = min(l1, nrows - 1);
-            {
+            if (l < lstop) {
+                // the loads of the next row are issued before the update of this one
                 const float4 *sp = cur + (l + 1) * sq;
                 float4 *o = nxt + l * sq;
                 const FacCoef<float> *cf = coef + l;
+                float4 pm = sp[0], pu = o[0];
+                float2 pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
+                float2 pe = *reinterpret_cast<const float2 *>(&sp[1].x);
+                int left = lstop - l;   // rows of the march still to do, this one included
                 auto row = [&](const Row2 &wn, Row2 &wc, Row2 &ws) {
-                    load_row(sp, ws);
+                    row_from(pw, pm, pe, ws);
+                    float4 u = pu;
+                    if (--left > 0) {
+                        sp += sq;
+                        pm = sp[0];
+                        pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
+                        pe = *reinterpret_cast<const float2 *>(&sp[1].x);
+                        pu = o[sq];
+                    }
                     south(wc, ws);
                     const FacCoef<float> K = *cf;
-                    float4 u = *o;
                     pair_update(K, wn, wc, ws, u);
-                    if (kind) absorbing(K.cp, K.cs, wn, wc, false, kind, u);
+                    if (kind) absorbing(K.cp, K.cs, u, wc, false, kind, u);
                     *o = u;
-                    sp += sq;
                     o += sq;
                     cf++;
                 };
@@ -301,12 +313,14 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 float4 *o = nxt + l * sq;
                 float4 u = *o;
                 if (j0 + l == g.nz - 1) {
-                    absorbing(K.cp, K.cs, rn, rc, true, kind, u);
+                    const float4 nv = l > 0 ? cur[(l - 1) * sq]
+                                            : ld_cluster4(remote_addr(smem_addr(cur + (R - 1) * sq), rank - 1));
+                    absorbing(K.cp, K.cs, nv, rc, true, kind, u);
                 } else {
                     load_row_remote(cur, rank + 1, rs);
                     south(rc, rs);
                     pair_update(K, rn, rc, rs, u);
-                    if (kind) absorbing(K.cp, K.cs, rn, rc, false, kind, u);
+                    if (kind) absorbing(K.cp, K.cs, u, rc, false, kind, u);
                 }
                 *o = u;
                 rn = rc;
