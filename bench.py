@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "plain_small", "layered", "design_sweep", "paper_scenarios"])
+                    choices=["batched", "plain_small", "layered", "design_sweep", "paper_scenarios",
+                             "paper_study"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -73,6 +74,11 @@ def parse():
     ap.add_argument("--jacobian", default="pairs", choices=["pairs", "difference"])
     ap.add_argument("--no-difference", action="store_true",
                     help="skip the extra measurement of the difference-form Jacobian")
+    ap.add_argument("--study-levels", type=int, default=20,
+                    help="paper_study: sparse grids 5 .. 5 + n - 1 (20: the paper's 351 .. 271857 nodes)")
+    ap.add_argument("--study-realisations", type=int, default=10)
+    ap.add_argument("--dlmc-sizes", type=lambda v: [int(x) for x in v.split(",")],
+                    default=[256, 1024, 4096, 16384, 65536])
     ap.add_argument("--serving", action="store_true",
                     help="serving benchmark: Poisson arrivals of mixed EIG requests")
     ap.add_argument("--requests", type=int, default=32)
@@ -591,6 +597,116 @@ def run_paper_scenarios(args, rank, world, local):
         print(json.dumps(out))
 
 
+def _fit_rate(n, err):
+    """Convergence rate r of err ~ n^-r by least squares in log-log."""
+    n, err = np.asarray(n, float), np.asarray(err, float)
+    ok = err > 0
+    if ok.sum() < 2:
+        return None
+    return float(-np.polyfit(np.log(n[ok]), np.log(err[ok]), 1)[0])
+
+
+def run_paper_study(args, rank, world, local):
+    """Sec. 4.3-4.4 on the model problem: three unknowns (theta_2 depth, theta_4 omega,
+    theta_5 m_xx), the other four known; observed for T = 1.25 s at x_1 = -9000 m and
+    1000 m; C_eps = 1e-4 I.
+    (a) Laplace EIG (Thm 4 on the unknowns, sensitivity solves, FP32 stencil) on the
+        twenty sparse grids of Sec. 4.3 (351 ... 271857 nodes) and on Monte Carlo samples
+        M = 1e2 ... 1e5 (ten realisations each); relative errors and fitted rates (the paper:
+        0.40 sparse, 0.49 MC).
+    (b) Double-loop Monte Carlo estimate of the definition (FP64 seismograms, N = M outer /
+        inner samples, independent and reused) against the finest Laplace value (the paper:
+        within 4%)."""
+    import torch
+    import paper_1502_07873_gb300 as P
+    from paper_1502_07873_gb300 import build as B
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = W.paper_study_model()
+    sigma = 0.01
+    unknown = list(W.PAPER_STUDY_UNKNOWN)
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+    chunk = 4096
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=7 * chunk)
+    ctx.jacobian = P.OED_JAC_SENSITIVITY
+    tuning = ctx.autotune(7 * chunk, stream=stream)
+
+    def laplace(theta, wts):
+        n = theta.shape[0]
+        th = torch.tensor(theta, device=dev)
+        H = torch.empty((n, 7, 7), dtype=torch.float64, device=dev)
+        eig = torch.empty(1, dtype=torch.float64, device=dev)
+        nb = torch.empty(1, dtype=torch.int32, device=dev)
+        P.oed_hessian(ctx, th, w.prior_lo, w.prior_hi, w.rel_step, sigma, H, stream=stream)
+        P.oed_eig_subset(ctx, H, torch.tensor(wts, device=dev), w.prior_lo, w.prior_hi, unknown, eig,
+                         n_bad=nb, stream=stream)
+        return float(eig.item()), int(nb.item())
+
+    t0 = time.perf_counter()
+    sparse = []
+    for L in range(5, 5 + args.study_levels):
+        x, wt = P.oed_nodes_smolyak(3, L, lo[unknown], hi[unknown])
+        th = np.tile(np.array(W.PAPER_STUDY_KNOWN), (x.shape[0], 1))
+        th[:, unknown] = x
+        e, nb = laplace(th, wt)
+        sparse.append([int(x.shape[0]), e, nb])
+    t_sparse = time.perf_counter() - t0
+    ref = sparse[-1][1]
+    sp_err = [[sparse[i][0], abs(sparse[i + 1][1] - sparse[i][1]) / abs(sparse[i + 1][1])]
+              for i in range(len(sparse) - 1)]
+    t0 = time.perf_counter()
+    mc = []
+    rng = np.random.default_rng(43)
+    for M in (100, 1000, 10000, 50000, 100000):
+        vals = [laplace(W.paper_study_thetas(rng.random((M, 3))), np.full(M, 1.0 / M))[0]
+                for _ in range(args.study_realisations)]
+        # relative error of one estimate: the spread of the realisations over their mean
+        mc.append([M, float(np.mean(vals)), float(np.std(vals)), float(np.std(vals) / abs(np.mean(vals)))])
+    t_mc = time.perf_counter() - t0
+    ref = mc[-1][1]   # the most accurate Laplace value: 10 realisations of M = 1e5
+    # (b) double-loop Monte Carlo, FP64 seismograms
+    ctx64 = P.Context(P.problem_from_workload(w, P.OED_FP64), max_solves=chunk)
+    D = w.nlevels * w.nrec * 2
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(44)
+    dl = []
+    for N in args.dlmc_sizes:
+        r = np.random.default_rng(1000 + N)
+        th_o = torch.tensor(W.paper_study_thetas(r.random((N, 3))), device=dev)
+        th_i = torch.tensor(W.paper_study_thetas(r.random((N, 3))), device=dev)
+        g_o = torch.empty((N, D), dtype=torch.float64, device=dev)
+        g_i = torch.empty((N, D), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for a in range(0, N, chunk):
+            b = min(N, a + chunk)
+            P.oed_forward(ctx64, th_o[a:b], g_o[a:b], stream=stream)
+            P.oed_forward(ctx64, th_i[a:b], g_i[a:b], stream=stream)
+        eps = sigma * torch.randn((N, D), dtype=torch.float64, device=dev, generator=gen)
+        le = torch.empty(N, dtype=torch.float64, device=dev)
+        e_ind = torch.empty(1, dtype=torch.float64, device=dev)
+        e_re = torch.empty(1, dtype=torch.float64, device=dev)
+        P.oed_dlmc(g_o, eps, g_i, sigma, le, e_ind, stream=stream)
+        P.oed_dlmc(g_o, eps, g_o, sigma, le, e_re, stream=stream)
+        torch.cuda.synchronize()
+        dl.append([N, float(e_ind.item()), float(e_re.item()), time.perf_counter() - t1])
+    out = {"metric": "Sec. 4.3-4.4: Laplace EIG convergence and Laplace vs double-loop MC",
+           "workload": w.name, "unknown": ["theta_2 (depth)", "theta_4 (omega)", "theta_5 (m_xx)"],
+           "sigma": sigma, "stencil_kernel": kernel_label(tuning),
+           "laplace_sparse": sparse, "sparse_rel_err": sp_err,
+           "sparse_rate": _fit_rate([e[0] for e in sp_err], [e[1] for e in sp_err]),
+           "laplace_mc": mc, "mc_rate": _fit_rate([m[0] for m in mc], [m[3] for m in mc]),
+           "laplace_reference": ref, "laplace_reference_from": "mean of the M = 1e5 realisations",
+           "seconds_sparse": t_sparse, "seconds_mc": t_mc,
+           "dlmc_columns": ["N = M", "independent inner samples", "inner = outer samples (reused)",
+                            "seconds"],
+           "dlmc": dl, "dlmc_reused_rel_to_laplace": [(d[2] - ref) / abs(ref) for d in dl]}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 SERVING_GRIDS = ((201, 101, 10.0), (401, 201, 5.0))
 
 
@@ -681,6 +797,9 @@ def main():
         return
     if args.workload == "paper_scenarios" and args.impl == "ours":
         run_paper_scenarios(args, rank, world, local)
+        return
+    if args.workload == "paper_study" and args.impl == "ours":
+        run_paper_study(args, rank, world, local)
         return
     if args.workload in ("layered", "design_sweep") and args.impl == "ours":
         run_other_workload(args, rank, world, local)

@@ -202,6 +202,37 @@ int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, cons
 int oed_eig(oed_ctx *ctx, const double *H, int n, const double *w, const double *lo,
             const double *hi, double *eig, double *dkl, int *status, int *n_bad, void *stream);
 
+/* The same for a problem in which only some parameters are unknown and the others
+ * are known (the three-parameter studies of Sec. 4.3 and 4.4): the Laplace gain of
+ * Thm 4 with N_theta = k, the number of unknowns,
+ *   D_i = 1/2 log det H_FF - k/2 (1 + log 2 pi) + sum_{j in F} log(hi_j - lo_j),
+ * where H_FF is the sub-block of H_1 over the unknown set F (rows and columns of
+ * known parameters drop out; the scaling and Cholesky act on H_FF).
+ *   param_mask  bit j set = parameter j (paper order) is unknown; 1..127
+ *               (127 is oed_eig).  Other arguments as for oed_eig; lo, hi are
+ *               read only at the unknown indices.
+ * Errors: OED_EINVAL for a mask outside 1..127 or hi_j <= lo_j at an unknown j. */
+int oed_eig_subset(oed_ctx *ctx, const double *H, int n, const double *w, const double *lo,
+                   const double *hi, int param_mask, double *eig, double *dkl, int *status,
+                   int *n_bad, void *stream);
+
+/* Double-loop (nested) Monte Carlo estimate of the expected information gain:
+ * Eq. expected_I sampled directly, the estimator the Laplace method replaces
+ * (Sec. 4.4 compares the two).  With y_n = g_outer[n] + eps[n] and noise sigma^2 I,
+ *   log_ev[n] = log( (1/M) sum_m exp(-|y_n - g_inner[m]|^2 / (2 sigma^2)) )
+ *   eig       = (1/N) sum_n ( -|eps_n|^2 / (2 sigma^2) - log_ev[n] )
+ * (the Gaussian normalising constant cancels).  FP64 throughout; distances are
+ * summed from the differences (no |y|^2 + |g|^2 - 2 y.g expansion).
+ *   g_outer  device [N][D]  noise-free data of the outer samples, e.g. seismograms
+ *                           from oed_forward (D = (nsteps+1) * nrec * 2)
+ *   eps      device [N][D]  the noise realisations (the caller draws them)
+ *   g_inner  device [M][D]  data of the inner (evidence) samples; passing the
+ *                           outer set again gives the sample-reusing variant
+ *   log_ev   device [N]; eig device [1] or NULL
+ * N, M, D >= 1, sigma > 0, else OED_EINVAL.  Asynchronous on `stream`. */
+int oed_dlmc(const double *g_outer, const double *eps, int N, const double *g_inner, int M, int D,
+             double sigma, double *log_ev, double *eig, void *stream);
+
 /* EIG of many receiver designs from per-receiver partial Hessians (H_1 is
  * additive over receivers and levels, Appendix C):
  *   H_d(theta_i) = sum_{r : mask[d][r] != 0} H_rec[i][r][win]

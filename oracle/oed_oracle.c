@@ -23,6 +23,10 @@
  *   ref_scaled_logdet  S = sqrt(diag H_1), S^-T H_1 S^-1      (Sec. 3.3.3)
  *   ref_dkl            D_KL-hat                               (Thm 4, Eq. DKL_hat)
  *   ref_eig            sum_i w_i D_KL-hat(theta_i)            (Eqs. intpoly, mcs)
+ *   ref_scaled_logdet_sub  the same log-det for the unknown parameters of a
+ *                      subset (the known ones drop out)       (Sec. 4.3, 4.4)
+ *   ref_dlmc           double-loop Monte Carlo EIG, the direct sampling of
+ *                      the definition                         (Eq. expected_I, Sec. 4.4)
  *
  * Readings of points the paper leaves open (the paper cites Nilsson et al. for
  * A_h and B_h without printing them):
@@ -577,4 +581,79 @@ int ref_eig(int nx, int nz, double h, double dt, int nsteps, const double *lam,
     free(D);
     free(st);
     return used;
+}
+
+/* ---------------------------------------------------------------------------
+ * Scaled log-det of the sub-block of H_1 (7x7, row-major) over the parameters
+ * whose bit is set in mask (Sec. 3.3.3 applied to the unknown parameters only;
+ * the known parameters are fixed and their rows and columns drop out).
+ * Returns 0, or 1 if the sub-block is not positive definite.
+ * ------------------------------------------------------------------------- */
+int ref_scaled_logdet_sub(const double *H, int mask, double *logdet)
+{
+    int idx[NT], k = 0;
+    for (int j = 0; j < NT; j++)
+        if (mask >> j & 1) idx[k++] = j;
+    if (k == 0) return 1;
+    double S[NT], L[NT * NT];
+    for (int a = 0; a < k; a++) {
+        double d = H[idx[a] * NT + idx[a]];
+        if (!(d > 0.0)) return 1;
+        S[a] = sqrt(d);
+    }
+    memset(L, 0, sizeof(L));
+    for (int j = 0; j < k; j++) {
+        double s = H[idx[j] * NT + idx[j]] / (S[j] * S[j]);
+        for (int c = 0; c < j; c++) s -= L[j * NT + c] * L[j * NT + c];
+        if (!(s > 0.0)) return 1;
+        L[j * NT + j] = sqrt(s);
+        for (int i = j + 1; i < k; i++) {
+            double t = H[idx[i] * NT + idx[j]] / (S[i] * S[j]);
+            for (int c = 0; c < j; c++) t -= L[i * NT + c] * L[j * NT + c];
+            L[i * NT + j] = t / L[j * NT + j];
+        }
+    }
+    double ld = 0.0;
+    for (int a = 0; a < k; a++) ld += 2.0 * log(S[a]) + 2.0 * log(L[a * NT + a]);
+    *logdet = ld;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Double-loop Monte Carlo estimate of the expected information gain (Eq.
+ * expected_I by direct sampling; Sec. 4.4).  Outer samples: y_n = g_out[n] +
+ * eps[n] (n < N), inner samples g_in[m] (m < M), each a vector of D data values,
+ * Gaussian noise sigma^2 I:
+ *   log_ev[n] = log( (1/M) sum_m exp(-|y_n - g_in[m]|^2 / (2 sigma^2)) )
+ *   *eig      = (1/N) sum_n ( -|eps_n|^2 / (2 sigma^2) - log_ev[n] )
+ * The Gaussian normalising constant cancels between the two terms.  The sum of
+ * exponentials is taken relative to its largest term (log-sum-exp) so it does
+ * not underflow; otherwise the definition is written out as it reads.
+ * ------------------------------------------------------------------------- */
+void ref_dlmc(const double *g_out, const double *eps, int N, const double *g_in, int M, int D,
+              double sigma, double *log_ev, double *eig)
+{
+    const double s2 = 2.0 * sigma * sigma;
+    double *l = malloc(sizeof(double) * (M > 0 ? M : 1));
+    double total = 0.0;
+    for (int n = 0; n < N; n++) {
+        double lmax = -INFINITY;
+        for (int m = 0; m < M; m++) {
+            double q = 0.0;
+            for (int d = 0; d < D; d++) {
+                double r = g_out[(size_t)n * D + d] + eps[(size_t)n * D + d] - g_in[(size_t)m * D + d];
+                q += r * r;
+            }
+            l[m] = -q / s2;
+            if (l[m] > lmax) lmax = l[m];
+        }
+        double sum = 0.0;
+        for (int m = 0; m < M; m++) sum += exp(l[m] - lmax);
+        log_ev[n] = lmax + log(sum) - log((double)M);
+        double e2 = 0.0;
+        for (int d = 0; d < D; d++) e2 += eps[(size_t)n * D + d] * eps[(size_t)n * D + d];
+        total += -e2 / s2 - log_ev[n];
+    }
+    *eig = total / N;
+    free(l);
 }

@@ -73,6 +73,10 @@ def lib():
         L.ref_eig.argtypes = [c_int, c_int, c_double, c_double, c_int, dp, dp, dp, c_int, ip,
                               c_int, dp, dp, dp, dp, c_double, c_double, c_int, dp, dp, ip, dp]
         L.ref_eig.restype = c_int
+        L.ref_scaled_logdet_sub.argtypes = [dp, c_int, dp]
+        L.ref_scaled_logdet_sub.restype = c_int
+        L.ref_dlmc.argtypes = [dp, dp, c_int, dp, c_int, c_int, c_double, dp, dp]
+        L.ref_dlmc.restype = None
         _lib = L
     return _lib
 
@@ -219,6 +223,30 @@ def scaled_logdet(H):
     Ht = np.zeros(49)
     rc = lib().ref_scaled_logdet(_pd(Hd), ctypes.byref(ld), _pd(Ht))
     return ld.value, Ht.reshape(7, 7), rc == 0
+
+
+def scaled_logdet_sub(H, free):
+    """(logdet, ok) of the sub-block of H over the unknown parameters `free` (indices)."""
+    mask = 0
+    for j in free:
+        mask |= 1 << int(j)
+    ld = ctypes.c_double()
+    rc = lib().ref_scaled_logdet_sub(_pd(_d(H).ravel()), int(mask), ctypes.byref(ld))
+    return ld.value, rc == 0
+
+
+def dlmc(g_outer, eps, g_inner, sigma):
+    """Double-loop Monte Carlo EIG (Eq. expected_I by direct sampling, Sec. 4.4):
+    returns (log_ev[N], eig).  g_outer, eps: [N][D]; g_inner: [M][D]."""
+    go = _d(g_outer).reshape(len(g_outer), -1)
+    e = _d(eps).reshape(go.shape)
+    gi = _d(g_inner).reshape(len(g_inner), -1)
+    assert gi.shape[1] == go.shape[1]
+    N, D = go.shape
+    le = np.zeros(N)
+    eig = ctypes.c_double()
+    lib().ref_dlmc(_pd(go), _pd(e), N, _pd(gi), gi.shape[0], D, float(sigma), _pd(le), ctypes.byref(eig))
+    return le, eig.value
 
 
 def dkl(logdet: float, n: int, log_prior_density: float) -> float:

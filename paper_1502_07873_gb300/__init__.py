@@ -31,7 +31,7 @@ SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_resident_min_cluster", "oed_set_jacobian", "oed_get_jacobian",
            "oed_gauss_newton_noalloc", "oed_server_create", "oed_server_request_bytes",
            "oed_server_submit", "oed_server_poll", "oed_server_wait", "oed_server_stats",
-           "oed_server_destroy")
+           "oed_server_destroy", "oed_eig_subset", "oed_dlmc")
 
 
 class OedError(RuntimeError):
@@ -87,6 +87,8 @@ def library():
         "oed_hessian": (i, [vp, vp, i, dp, dp, d, d, ip, i, vp, vp, vp, vp]),
         "oed_eig": (i, [vp, vp, i, vp, dp, dp, vp, vp, vp, vp, vp]),
         "oed_eig_designs": (i, [vp, vp, i, i, i, i, vp, i, vp, dp, dp, vp, vp, vp]),
+        "oed_eig_subset": (i, [vp, vp, i, vp, dp, dp, i, vp, vp, vp, vp, vp]),
+        "oed_dlmc": (i, [vp, vp, i, vp, i, i, d, vp, vp, vp]),
         "oed_nodes_mc": (i, [vp, i, dp, dp, vp, vp, vp]),
         "oed_nodes_smolyak": (i, [i, i, dp, dp, i, dp, dp, ip]),
         "oed_eig_host": (i, [vp, dp, dp, i, dp, dp, d, d, dp, dp, ip]),
@@ -278,6 +280,34 @@ def oed_eig(ctx: Optional[Context], H, w, lo, hi, eig, dkl=None, status=None, n_
     rc = library().oed_eig(h, _ptr(H), n, _ptr(w), _darr(lo), _darr(hi), _ptr(eig), _ptr(dkl),
                            _ptr(status), _ptr(n_bad), _stream(stream))
     _check(h, rc, "oed_eig")
+    return eig
+
+
+def oed_eig_subset(ctx: Optional[Context], H, w, lo, hi, free, eig, dkl=None, status=None,
+                   n_bad=None, stream=None):
+    """EIG of the problem whose unknown parameters are the indices in `free` (the others
+    known): D_KL-hat from the sub-block of H_1, into eig[1] (device)."""
+    mask = 0
+    for j in free:
+        mask |= 1 << int(j)
+    n = H.shape[0]
+    h = ctx.handle if ctx is not None else None
+    rc = library().oed_eig_subset(h, _ptr(H), n, _ptr(w), _darr(lo), _darr(hi), mask, _ptr(eig),
+                                  _ptr(dkl), _ptr(status), _ptr(n_bad), _stream(stream))
+    _check(h, rc, "oed_eig_subset")
+    return eig
+
+
+def oed_dlmc(g_outer, eps, g_inner, sigma, log_ev, eig=None, stream=None):
+    """Double-loop Monte Carlo EIG: y_n = g_outer[n] + eps[n] against the inner samples
+    g_inner (all device FP64, [N][D] / [M][D]); log_ev[N] and eig[1] (device)."""
+    N = g_outer.shape[0]
+    M = g_inner.shape[0]
+    D = g_outer[0].numel()
+    if g_inner[0].numel() != D or eps.shape[0] != N:
+        raise ValueError("oed_dlmc: shapes")
+    _check(None, library().oed_dlmc(_ptr(g_outer), _ptr(eps), N, _ptr(g_inner), M, D, float(sigma),
+                                    _ptr(log_ev), _ptr(eig), _stream(stream)), "oed_dlmc")
     return eig
 
 

@@ -491,15 +491,28 @@ static double log_volume(const double *lo, const double *hi)
     return v;
 }
 
-int oed_eig(oed_ctx *ctx, const double *H, int n, const double *w, const double *lo,
-            const double *hi, double *eig, double *dkl, int *status, int *n_bad, void *stream)
+int oed_eig_subset(oed_ctx *ctx, const double *H, int n, const double *w, const double *lo,
+                   const double *hi, int param_mask, double *eig, double *dkl, int *status, int *n_bad,
+                   void *stream)
 {
     if (n < 0 || (n > 0 && (!H || !w)) || !eig || !lo || !hi)
         return set_err(ctx, OED_EINVAL, "oed_eig: bad arguments");
-    for (int j = 0; j < kNT; j++)
+    if (param_mask < 1 || param_mask > 127)
+        return set_err(ctx, OED_EINVAL, "oed_eig_subset: param_mask must be in 1..127");
+    double logvol = 0.0;
+    for (int j = 0; j < kNT; j++) {
+        if (!(param_mask >> j & 1)) continue;
         if (!(hi[j] > lo[j])) return set_err(ctx, OED_EINVAL, "oed_eig: need hi > lo");
-    launch_eig(H, n, w, log_volume(lo, hi), eig, dkl, status, n_bad, (cudaStream_t)stream);
+        logvol += log(hi[j] - lo[j]);
+    }
+    launch_eig(H, n, w, logvol, param_mask, eig, dkl, status, n_bad, (cudaStream_t)stream);
     return cuda_err(ctx, cudaGetLastError(), "oed_eig");
+}
+
+int oed_eig(oed_ctx *ctx, const double *H, int n, const double *w, const double *lo,
+            const double *hi, double *eig, double *dkl, int *status, int *n_bad, void *stream)
+{
+    return oed_eig_subset(ctx, H, n, w, lo, hi, 127, eig, dkl, status, n_bad, stream);
 }
 
 int oed_eig_designs(oed_ctx *ctx, const double *H_rec, int n, int nrec, int nwin, int win,

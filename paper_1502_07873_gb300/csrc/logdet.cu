@@ -12,21 +12,22 @@
 namespace oed {
 
 // Returns 0 and *logdet, or 1 if H is not positive definite (or not finite).
-// H is read through an accessor so both the full 7x7 and the packed 28 forms work.
-template <typename Get>
-__device__ int scaled_logdet7(Get Hij, double *logdet)
+// H is read through an accessor so both the full 7x7 and the packed 28 forms work;
+// K is the order (7, or the number of unknown parameters of a subset).
+template <int K, typename Get>
+__device__ int scaled_logdet_k(Get Hij, double *logdet)
 {
-    double S[kNT], L[kNT][kNT];
+    double S[K], L[K][K];
     double ld = 0.0;
 #pragma unroll
-    for (int i = 0; i < kNT; i++) {
+    for (int i = 0; i < K; i++) {
         const double d = Hij(i, i);
         if (!(d > 0.0) || !isfinite(d)) return 1;
         S[i] = sqrt(d);
         ld += log(d);
     }
 #pragma unroll
-    for (int j = 0; j < kNT; j++) {
+    for (int j = 0; j < K; j++) {
         double s = Hij(j, j) / (S[j] * S[j]);
 #pragma unroll
         for (int k = 0; k < j; k++) s -= L[j][k] * L[j][k];
@@ -35,7 +36,7 @@ __device__ int scaled_logdet7(Get Hij, double *logdet)
         L[j][j] = ljj;
         ld += 2.0 * log(ljj);
 #pragma unroll
-        for (int i = j + 1; i < kNT; i++) {
+        for (int i = j + 1; i < K; i++) {
             double t = Hij(i, j) / (S[i] * S[j]);
 #pragma unroll
             for (int k = 0; k < j; k++) t -= L[i][k] * L[j][k];
@@ -44,6 +45,28 @@ __device__ int scaled_logdet7(Get Hij, double *logdet)
     }
     *logdet = ld;
     return 0;
+}
+
+template <typename Get>
+__device__ int scaled_logdet7(Get Hij, double *logdet)
+{
+    return scaled_logdet_k<kNT>(Hij, logdet);
+}
+
+// log det of the sub-block of the unknown parameters idx[0..k) of a 7x7 H
+template <typename Get>
+__device__ int scaled_logdet_sub(Get Hij, const int *idx, int k, double *logdet)
+{
+    auto sub = [&](int a, int b) { return Hij(idx[a], idx[b]); };
+    switch (k) {
+    case 1: return scaled_logdet_k<1>(sub, logdet);
+    case 2: return scaled_logdet_k<2>(sub, logdet);
+    case 3: return scaled_logdet_k<3>(sub, logdet);
+    case 4: return scaled_logdet_k<4>(sub, logdet);
+    case 5: return scaled_logdet_k<5>(sub, logdet);
+    case 6: return scaled_logdet_k<6>(sub, logdet);
+    default: return scaled_logdet_k<7>(sub, logdet);
+    }
 }
 
 __device__ __forceinline__ int upper_index(int a, int b)
@@ -56,18 +79,19 @@ __device__ __forceinline__ int upper_index(int a, int b)
     return a * kNT - a * (a - 1) / 2 + (b - a);
 }
 
-// D_KL-hat from log det H_1 (N = 7): 1/2 logdet - 7/2 (log 2 pi + 1) + logvol
-__device__ __forceinline__ double dkl_from_logdet(double ld, double logvol)
+// D_KL-hat from log det H_1 of k unknown parameters: 1/2 logdet - k/2 (log 2 pi + 1) + logvol
+__device__ __forceinline__ double dkl_from_logdet(double ld, double logvol, int k = kNT)
 {
-    const double c = 3.5 * (1.8378770664093453 + 1.0);   // 7/2 (log(2 pi) + 1)
+    const double c = 0.5 * k * (1.8378770664093453 + 1.0);   // k/2 (log(2 pi) + 1)
     return 0.5 * ld - c + logvol;
 }
 
 // Whole quadrature in one block, deterministic: thread t takes the contiguous node
 // slice [t*per, (t+1)*per), computes each node's log-determinant and gain in order,
 // then the block adds the per-thread sums with a fixed tree.
+// pmask: bit j set = parameter j unknown (the others are known and drop out).
 __global__ void __launch_bounds__(1024) k_eig(const double *__restrict__ H, int n,
-                                              const double *__restrict__ w, double logvol,
+                                              const double *__restrict__ w, double logvol, int pmask,
                                               double *__restrict__ eig, double *__restrict__ dkl,
                                               int *__restrict__ status, int *__restrict__ n_bad)
 {
@@ -75,13 +99,18 @@ __global__ void __launch_bounds__(1024) k_eig(const double *__restrict__ H, int 
     __shared__ int sb[1024];
     const int t = threadIdx.x, T = blockDim.x;
     const int per = (n + T - 1) / T;
+    int idx[kNT], k = 0;
+#pragma unroll
+    for (int j = 0; j < kNT; j++)
+        if (pmask >> j & 1) idx[k++] = j;
     double v = 0.0;
     int b = 0;
     for (int i = t * per; i < (t + 1) * per && i < n; i++) {
         const double *h = H + (size_t)i * 49;
         double ld = 0.0;
-        const int bad = scaled_logdet7([&](int x, int y) { return h[x * 7 + y]; }, &ld);
-        const double D = bad ? 0.0 : dkl_from_logdet(ld, logvol);
+        const int bad = k == kNT ? scaled_logdet7([&](int x, int y) { return h[x * 7 + y]; }, &ld)
+                                 : scaled_logdet_sub([&](int x, int y) { return h[x * 7 + y]; }, idx, k, &ld);
+        const double D = bad ? 0.0 : dkl_from_logdet(ld, logvol, k);
         if (!bad) v += w[i] * D;
         b += bad;
         if (dkl) dkl[i] = D;
@@ -171,10 +200,10 @@ __global__ void k_nodes_mc_v(const double *__restrict__ u, int M, LoHi lh, doubl
     if (j == 0) w[k / kNT] = 1.0 / M;
 }
 
-void launch_eig(const double *H, int n, const double *w, double logvol, double *eig, double *dkl,
-                int *status, int *n_bad, cudaStream_t s)
+void launch_eig(const double *H, int n, const double *w, double logvol, int pmask, double *eig,
+                double *dkl, int *status, int *n_bad, cudaStream_t s)
 {
-    k_eig<<<1, 1024, 0, s>>>(H, n, w, logvol, eig, dkl, status, n_bad);
+    k_eig<<<1, 1024, 0, s>>>(H, n, w, logvol, pmask, eig, dkl, status, n_bad);
 }
 
 void launch_eig_designs(const double *H_rec, int n, int nrec, int nwin, int win,

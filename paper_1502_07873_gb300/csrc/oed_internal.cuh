@@ -169,7 +169,7 @@ void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double s
                     double *H_rec, int *status, cudaStream_t s);
 
 // logdet.cu
-void launch_eig(const double *H, int n, const double *w, double logvol, double *eig,
+void launch_eig(const double *H, int n, const double *w, double logvol, int pmask, double *eig,
                 double *dkl, int *status, int *n_bad, cudaStream_t s);
 void launch_eig_designs(const double *H_rec, int n, int nrec, int nwin, int win,
                         const unsigned char *mask, int ndesign, const double *w, double logvol,

@@ -214,5 +214,28 @@ def paper_scenarios():
     return out
 
 
+# Sec. 4.3-4.4: three unknowns (theta_2 = depth, theta_4 = omega, theta_5 = m_xx), the other
+# four known: theta_1 = -1000 m (x = 9000 m here), theta_3 = 1 s, theta_6 = theta_7 = 1e14.
+PAPER_STUDY_UNKNOWN = (1, 3, 4)
+PAPER_STUDY_KNOWN = (9000.0, 2000.0, 1.0, 4.0, 1e14, 1e14, 1e14)   # unknown entries unused
+
+
+def paper_study_model() -> Workload:
+    """Sec. 4.4's setting: the model problem observed for T = 1.25 s (50 steps) at two
+    receivers, x_1 = -9000 m and x_1 = 1000 m (x = 1000 m and 11000 m here)."""
+    w = paper_model()
+    return Workload(name="paper_loh_101x76_50steps_2rec", nx=w.nx, nz=w.nz, h=w.h, nsteps=50, dt=w.dt,
+                    layers=w.layers, rec_ix=[5, 55], prior_lo=w.prior_lo, prior_hi=w.prior_hi)
+
+
+def paper_study_thetas(u: np.ndarray) -> np.ndarray:
+    """Full parameter vectors from uniform variates u[n][3] of the three unknowns."""
+    lo, hi = np.array(PAPER_PRIOR_LO), np.array(PAPER_PRIOR_HI)
+    th = np.tile(np.array(PAPER_STUDY_KNOWN), (u.shape[0], 1))
+    for k, j in enumerate(PAPER_STUDY_UNKNOWN):
+        th[:, j] = lo[j] + (hi[j] - lo[j]) * u[:, k]
+    return th
+
+
 ALL = {"plain_small": plain_small, "batched": batched, "layered": layered,
        "design_sweep": design_sweep}
