@@ -27,6 +27,12 @@
  *                      subset (the known ones drop out)       (Sec. 4.3, 4.4)
  *   ref_dlmc           double-loop Monte Carlo EIG, the direct sampling of
  *                      the definition                         (Eq. expected_I, Sec. 4.4)
+ *   ref_adjoint        the dual problem: gradient of sum_m w^m . g^m with respect
+ *                      to every forcing value, by the transposed scheme
+ *                                                             (Eq. Dual_problems)
+ *   ref_hessian_ii     H_II and the cost gradient from one primal and one dual
+ *                      solve                                  (Alg. 1 steps 6-10,
+ *                                                             Eq. H2_numerics, Thm 2)
  *
  * Readings of points the paper leaves open (the paper cites Nilsson et al. for
  * A_h and B_h without printing them):
@@ -109,6 +115,29 @@ void ref_delta_1d_dxs(double a, double h, double *dd, double *ddp)
     ddp[3] = (-4.0 / 3.0 + a - 23.0 * a2 - 10.0 * Rp) / h3;
     ddp[4] = (1.0 / 12.0 - a / 2.0 + 12.0 * a2 + 5.0 * Rp) / h3;
     ddp[5] = (-5.0 * a2 / 2.0 - Rp) / h3;
+}
+
+/* Second derivatives of the same weights with respect to x_s (Alg. 1 step 9: the
+ * forcing's second derivatives, which exist because the regularised delta is C^2
+ * in x_s): (1/h^2) d^2/dalpha^2 of each printed polynomial. */
+void ref_delta_1d_dxs2(double a, double h, double *dd, double *ddp)
+{
+    double a2 = a * a, a3 = a2 * a, a4 = a3 * a, a5 = a4 * a, a6 = a5 * a, a7 = a6 * a;
+    double Ppp = 100.0 * a3 / 3.0 - 35.0 * a4 / 4.0 - 119.0 * a5 / 2.0 + 63.0 * a6 - 18.0 * a7;
+    double Rpp = -25.0 * a2 - 15.0 * a3 + 295.0 * a4 / 2.0 - 168.0 * a5 + 56.0 * a6;
+    double h3 = h * h * h, h4 = h3 * h;
+    dd[0] = (-1.0 / 12.0 - a / 2.0 - 19.0 * a2 / 2.0 + Ppp) / h3;
+    dd[1] = (4.0 / 3.0 + a + 48.0 * a2 - 5.0 * Ppp) / h3;
+    dd[2] = (-5.0 / 2.0 - 97.0 * a2 + 10.0 * Ppp) / h3;
+    dd[3] = (4.0 / 3.0 - a + 98.0 * a2 - 10.0 * Ppp) / h3;
+    dd[4] = (-1.0 / 12.0 + a / 2.0 - 99.0 * a2 / 2.0 + 5.0 * Ppp) / h3;
+    dd[5] = (10.0 * a2 - Ppp) / h3;
+    ddp[0] = (1.0 / 2.0 + 4.0 * a + Rpp) / h4;
+    ddp[1] = (-1.0 - 21.0 * a - 5.0 * Rpp) / h4;
+    ddp[2] = (44.0 * a + 10.0 * Rpp) / h4;
+    ddp[3] = (1.0 - 46.0 * a - 10.0 * Rpp) / h4;
+    ddp[4] = (-1.0 / 2.0 + 24.0 * a + 5.0 * Rpp) / h4;
+    ddp[5] = (-5.0 * a - Rpp) / h4;
 }
 
 /* Gaussian source time function of Sec. 4.1 with omega_0 read as omega_s. */
@@ -363,9 +392,28 @@ int ref_forward_forcing(int nx, int nz, double h, double dt, int nsteps, const d
  *   x_s, z_s: derivative of the delta / delta' weights; t_s, w_s: derivative of
  *   S(t); m_xx, m_xz, m_zz: the unit-moment patches.
  * ------------------------------------------------------------------------- */
+static int sens_solves(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                       const double *mu, const double *nu, int nrec, const int *rec_ix,
+                       const double *theta, double sigma, double *H, double *Jout);
+
 int ref_node_hessian_sens(int nx, int nz, double h, double dt, int nsteps, const double *lam,
                           const double *mu, const double *nu, int nrec, const int *rec_ix,
                           const double *theta, double sigma, double *H)
+{
+    return sens_solves(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, theta, sigma, H, NULL);
+}
+
+/* The Jacobian columns themselves, J[j][m][r][c] = dg_{m,r,c}/dtheta_j (step 3). */
+int ref_jacobian_sens(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                      const double *mu, const double *nu, int nrec, const int *rec_ix,
+                      const double *theta, double *J)
+{
+    return sens_solves(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, theta, 1.0, NULL, J);
+}
+
+static int sens_solves(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                       const double *mu, const double *nu, int nrec, const int *rec_ix,
+                       const double *theta, double sigma, double *H, double *Jout)
 {
     double xs = theta[0], zs = theta[1], mxx = theta[4], mxz = theta[5], mzz = theta[6];
     double qx = xs / h, qz = zs / h;
@@ -411,7 +459,7 @@ int ref_node_hessian_sens(int nx, int nz, double h, double dt, int nsteps, const
         rc |= ref_forward_forcing(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, kx - 2, kz - 2, px,
                                   pz, kind, theta[2], theta[3], gall + (size_t)j * nrow);
     }
-    if (rc == 0) {
+    if (rc == 0 && H) {
         double s2 = 1.0 / (sigma * sigma);
         for (int a = 0; a < NT * NT; a++) H[a] = 0.0;
         for (size_t k = 0; k < nrow; k++)
@@ -419,6 +467,7 @@ int ref_node_hessian_sens(int nx, int nz, double h, double dt, int nsteps, const
                 for (int b = 0; b < NT; b++)
                     H[a * NT + b] += s2 * gall[(size_t)a * nrow + k] * gall[(size_t)b * nrow + k];
     }
+    if (rc == 0 && Jout) memcpy(Jout, gall, sizeof(double) * nrow * NT);
     free(gall);
     return rc;
 }
@@ -656,4 +705,257 @@ void ref_dlmc(const double *g_out, const double *eps, int N, const double *g_in,
     }
     *eig = total / N;
     free(l);
+}
+
+/* ---------------------------------------------------------------------------
+ * Source time function and its derivatives with respect to (t_s, omega_s) up to
+ * second order (Alg. 1 steps 2 and 9), tau = t - t_s, L = log S:
+ *   dL/dt_s = w^2 tau, dL/dw = 1/w - w tau^2, d2L/dt_s2 = -w^2,
+ *   d2L/dt_s dw = 2 w tau, d2L/dw2 = -1/w^2 - tau^2,
+ * and d2S = S (dL dL + d2L).  out = (S, S_t, S_w, S_tt, S_tw, S_ww).
+ * ------------------------------------------------------------------------- */
+void ref_stf_derivs(double t, double ts, double w, double *out)
+{
+    double tau = t - ts, S = ref_stf(t, ts, w);
+    double Lt = w * w * tau, Lw = 1.0 / w - w * tau * tau;
+    out[0] = S;
+    out[1] = S * Lt;
+    out[2] = S * Lw;
+    out[3] = S * (Lt * Lt - w * w);
+    out[4] = S * (Lt * Lw + 2.0 * w * tau);
+    out[5] = S * (Lw * Lw - 1.0 / (w * w) - tau * tau);
+}
+
+/* ---------------------------------------------------------------------------
+ * The leap-frog step as a linear map on the state u = (u_x, u_z), 2 nx nz values:
+ *   u^{m+1} = B u^m + E u^{m-1} + F f^m   (Eq. Full_Disc)
+ * The j-th column of B (E, F) is the output of ref_step for a unit input at
+ * entry j of u^m (u^{m-1}, f^m) and zero elsewhere; its nonzero entries are kept.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n;
+    int *start;     /* [n + 1] */
+    int *row;
+    double *val;
+} ref_cols;
+
+static void probe_columns(const ref_grid *G, int which, ref_cols *C)
+{
+    int nx = G->nx, nz = G->nz;
+    size_t nn = (size_t)nx * nz;
+    int n = (int)(2 * nn);
+    double *in = calloc(2 * nn, sizeof(double)), *zero = calloc(2 * nn, sizeof(double));
+    double *out = calloc(2 * nn, sizeof(double));
+    size_t cap = (size_t)n * 24, used = 0;
+    C->n = n;
+    C->start = malloc(sizeof(int) * (n + 1));
+    C->row = malloc(sizeof(int) * cap);
+    C->val = malloc(sizeof(double) * cap);
+    for (int j = 0; j < n; j++) {
+        in[j] = 1.0;
+        const double *ux = which == 0 ? in : zero, *uz = which == 0 ? in + nn : zero + nn;
+        const double *uxm = which == 1 ? in : zero, *uzm = which == 1 ? in + nn : zero + nn;
+        const double *fx = which == 2 ? in : NULL, *fz = which == 2 ? in + nn : NULL;
+        ref_step(G, ux, uz, uxm, uzm, fx, fz, out, out + nn);
+        C->start[j] = (int)used;
+        for (int i = 0; i < n; i++) {
+            if (out[i] == 0.0) continue;
+            if (used == cap) {
+                cap *= 2;
+                C->row = realloc(C->row, sizeof(int) * cap);
+                C->val = realloc(C->val, sizeof(double) * cap);
+            }
+            C->row[used] = i;
+            C->val[used] = out[i];
+            used++;
+        }
+        in[j] = 0.0;
+    }
+    C->start[n] = (int)used;
+    free(in);
+    free(zero);
+    free(out);
+}
+
+static void free_cols(ref_cols *C)
+{
+    free(C->start);
+    free(C->row);
+    free(C->val);
+}
+
+/* (M^T v)_j = sum over the stored entries of column j of M_ij v_i */
+static void apply_transpose(const ref_cols *C, const double *v, double *out)
+{
+    for (int j = 0; j < C->n; j++) {
+        double s = 0.0;
+        for (int k = C->start[j]; k < C->start[j + 1]; k++) s += C->val[k] * v[C->row[k]];
+        out[j] = s;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Forward solve driven by a full forcing sequence f[m][c][nz][nx], m < nsteps
+ * (c = 0: x, 1: z), zero initial levels; receiver samples g[m][r][c], m <= nsteps.
+ * ------------------------------------------------------------------------- */
+void ref_forward_field(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                       const double *mu, const double *nu, int nrec, const int *rec_ix,
+                       const double *f, double *g)
+{
+    ref_grid G = {nx, nz, h, dt, lam, mu, nu};
+    size_t nn = (size_t)nx * nz;
+    double *ux = calloc(nn, sizeof(double)), *uz = calloc(nn, sizeof(double));
+    double *uxm = calloc(nn, sizeof(double)), *uzm = calloc(nn, sizeof(double));
+    double *uxn = calloc(nn, sizeof(double)), *uzn = calloc(nn, sizeof(double));
+    for (int r = 0; r < nrec; r++) g[r * 2] = g[r * 2 + 1] = 0.0;
+    for (int m = 0; m < nsteps; m++) {
+        const double *fm = f + (size_t)m * 2 * nn;
+        ref_step(&G, ux, uz, uxm, uzm, fm, fm + nn, uxn, uzn);
+        double *t;
+        t = uxm; uxm = ux; ux = uxn; uxn = t;
+        t = uzm; uzm = uz; uz = uzn; uzn = t;
+        for (int r = 0; r < nrec; r++) {
+            g[((size_t)(m + 1) * nrec + r) * 2 + 0] = ux[rec_ix[r]];
+            g[((size_t)(m + 1) * nrec + r) * 2 + 1] = uz[rec_ix[r]];
+        }
+    }
+    free(ux); free(uz); free(uxm); free(uzm); free(uxn); free(uzn);
+}
+
+/* ---------------------------------------------------------------------------
+ * The dual problem (Eq. Dual_problems): for the functional J = sum_{m=0}^{nsteps}
+ * sum_{r,c} w[m][r][c] g_{r,c}(t_m), the derivative of J with respect to every
+ * forcing value, gradf[m][c][nz][nx] = dJ/df^m (m < nsteps), from the transposed
+ * scheme run backwards:
+ *   lambda^m = R^T w^m + B^T lambda^{m+1} + E^T lambda^{m+2},  m = nsteps .. 1,
+ *   lambda^{nsteps+1} = lambda^{nsteps+2} = 0,   dJ/df^m = F^T lambda^{m+1},
+ * with R the receiver sampling.  B, E, F are read off the step by probing.
+ * ------------------------------------------------------------------------- */
+void ref_adjoint(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                 const double *mu, const double *nu, int nrec, const int *rec_ix, const double *w,
+                 double *gradf)
+{
+    ref_grid G = {nx, nz, h, dt, lam, mu, nu};
+    size_t nn = (size_t)nx * nz;
+    int n = (int)(2 * nn);
+    ref_cols B, E, F;
+    probe_columns(&G, 0, &B);
+    probe_columns(&G, 1, &E);
+    probe_columns(&G, 2, &F);
+    double *l1 = calloc(n, sizeof(double)), *l2 = calloc(n, sizeof(double));   /* m+1, m+2 */
+    double *l0 = calloc(n, sizeof(double)), *tmp = calloc(n, sizeof(double));
+    for (int m = nsteps; m >= 1; m--) {
+        apply_transpose(&B, l1, l0);
+        apply_transpose(&E, l2, tmp);
+        for (int j = 0; j < n; j++) l0[j] += tmp[j];
+        for (int r = 0; r < nrec; r++) {
+            l0[rec_ix[r]] += w[((size_t)m * nrec + r) * 2 + 0];
+            l0[nn + rec_ix[r]] += w[((size_t)m * nrec + r) * 2 + 1];
+        }
+        apply_transpose(&F, l0, gradf + (size_t)(m - 1) * n);
+        double *t = l2;
+        l2 = l1;
+        l1 = l0;
+        l0 = t;
+    }
+    free(l0); free(l1); free(l2); free(tmp);
+    free_cols(&B); free_cols(&E); free_cols(&F);
+}
+
+/* ---------------------------------------------------------------------------
+ * H_II and the cost gradient at theta for data y (Alg. 1 steps 6-10, Eq.
+ * H2_numerics, Thm 2's H_2), cost L = 1/2 sum_m sum_r r^T C^-1 r, r = y - g(theta),
+ * C = sigma^2 I:
+ *   step 6-7: primal solve, w = C^-1 r (the data-side derivative of L, sign aside),
+ *   step 8:   dual solve, dJ/df^m for J = sum w . g (ref_adjoint),
+ *   step 9-10: with f^m = S(t_m) P(x_s, z_s, M) on the 6x6 patch,
+ *     H_II[a][b] = - sum_m sum_patch dJ/df^m d2 f^m / dtheta_a dtheta_b,
+ *     grad[a]    = - sum_m sum_patch dJ/df^m d f^m / dtheta_a   (= dL/dtheta_a).
+ * d f / d(x_s, z_s) act on the delta / delta' weights of that axis, d f / dm_k
+ * select the k-th moment term, d f / d(t_s, w_s) act on S; d2 f / dm dm = 0.
+ * Returns 0, or -1 if the source patch leaves the interior.
+ * ------------------------------------------------------------------------- */
+int ref_hessian_ii(int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                   const double *mu, const double *nu, int nrec, const int *rec_ix,
+                   const double *theta, const double *y, double sigma, double *H2, double *grad)
+{
+    size_t nn = (size_t)nx * nz, nrow = (size_t)(nsteps + 1) * nrec * 2;
+    int i0, j0;
+    double px[36], pz[36];
+    if (ref_source_patch(theta, nx, nz, h, &i0, &j0, px, pz) != 0) return -1;
+    double *g = malloc(sizeof(double) * nrow), *w = malloc(sizeof(double) * nrow);
+    ref_forward(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, theta, g);
+    for (size_t k = 0; k < nrow; k++) w[k] = (y[k] - g[k]) / (sigma * sigma);
+    double *gf = malloc(sizeof(double) * (size_t)nsteps * 2 * nn);
+    ref_adjoint(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, w, gf);
+
+    /* weights of both axes and their first and second derivatives in x_s / z_s:
+     * W[axis][order][kind][a]: kind 0 delta, 1 delta' */
+    double W[2][3][2][6];
+    for (int axis = 0; axis < 2; axis++) {
+        double q = theta[axis] / h, al = q - floor(q);
+        ref_delta_1d(al, h, W[axis][0][0], W[axis][0][1]);
+        ref_delta_1d_dxs(al, h, W[axis][1][0], W[axis][1][1]);
+        ref_delta_1d_dxs2(al, h, W[axis][2][0], W[axis][2][1]);
+    }
+    /* P_c = sum_k m_k X_k Z_k: c = x: (m_xx: delta' x delta), (m_xz: delta x delta');
+     *                          c = z: (m_xz: delta' x delta), (m_zz: delta x delta') */
+    const int term_m[2][2] = {{4, 5}, {5, 6}};
+    const int term_xk[2][2] = {{1, 0}, {1, 0}};   /* kind of the x factor */
+    double Hs[NT * NT], gs[NT];
+    memset(Hs, 0, sizeof(Hs));
+    memset(gs, 0, sizeof(gs));
+    for (int m = 0; m < nsteps; m++) {
+        double sd[6];
+        ref_stf_derivs(m * dt, theta[2], theta[3], sd);
+        for (int c = 0; c < 2; c++)
+            for (int b = 0; b < 6; b++)
+                for (int a = 0; a < 6; a++) {
+                    double lamv = gf[(size_t)m * 2 * nn + (size_t)c * nn + (size_t)(j0 + b) * nx + (i0 + a)];
+                    if (lamv == 0.0) continue;
+                    /* dP/dtheta and d2P/dtheta2 of this node for the spatial parameters
+                     * (x_s, z_s, m_xx, m_xz, m_zz), S-derivatives for t_s, w_s */
+                    for (int p = 0; p < NT; p++)
+                        for (int q = p; q < NT; q++) {
+                            int ordx = (p == 0) + (q == 0), ordz = (p == 1) + (q == 1);
+                            int nt = (p == 2 || p == 3) + (q == 2 || q == 3);
+                            int nm = (p >= 4) + (q >= 4);
+                            if (nm == 2) continue;
+                            double P = 0.0;
+                            for (int k = 0; k < 2; k++) {
+                                int mk = term_m[c][k];
+                                double coef = theta[mk];
+                                if (nm == 1) coef = (p == mk || q == mk) ? 1.0 : 0.0;
+                                int xk = term_xk[c][k], zk = 1 - xk;
+                                P += coef * W[0][ordx][xk][a] * W[1][ordz][zk][b];
+                            }
+                            double S;
+                            if (nt == 0)
+                                S = sd[0];
+                            else if (nt == 1)
+                                S = ((p == 2 || q == 2) ? sd[1] : sd[2]);
+                            else
+                                S = (p == 2 && q == 2) ? sd[3] : ((p == 3 && q == 3) ? sd[5] : sd[4]);
+                            Hs[p * NT + q] += lamv * S * P;
+                        }
+                    for (int p = 0; p < NT; p++) {
+                        int ordx = (p == 0), ordz = (p == 1);
+                        double P = 0.0;
+                        for (int k = 0; k < 2; k++) {
+                            int mk = term_m[c][k];
+                            double coef = p >= 4 ? (p == mk ? 1.0 : 0.0) : theta[mk];
+                            int xk = term_xk[c][k], zk = 1 - xk;
+                            P += coef * W[0][ordx][xk][a] * W[1][ordz][zk][b];
+                        }
+                        double S = p == 2 ? sd[1] : (p == 3 ? sd[2] : sd[0]);
+                        gs[p] += lamv * S * P;
+                    }
+                }
+    }
+    for (int p = 0; p < NT; p++) {
+        if (grad) grad[p] = -gs[p];
+        for (int q = p; q < NT; q++) H2[p * NT + q] = H2[q * NT + p] = -Hs[p * NT + q];
+    }
+    free(g); free(w); free(gf);
+    return 0;
 }

@@ -77,6 +77,21 @@ def lib():
         L.ref_scaled_logdet_sub.restype = c_int
         L.ref_dlmc.argtypes = [dp, dp, c_int, dp, c_int, c_int, c_double, dp, dp]
         L.ref_dlmc.restype = None
+        L.ref_delta_1d_dxs2.argtypes = [c_double, c_double, dp, dp]
+        L.ref_delta_1d_dxs2.restype = None
+        L.ref_stf_derivs.argtypes = [c_double, c_double, c_double, dp]
+        L.ref_stf_derivs.restype = None
+        L.ref_jacobian_sens.argtypes = [c_int, c_int, c_double, c_double, c_int, dp, dp, dp, c_int, ip,
+                                        dp, dp]
+        L.ref_jacobian_sens.restype = c_int
+        L.ref_forward_field.argtypes = [c_int, c_int, c_double, c_double, c_int, dp, dp, dp, c_int, ip,
+                                        dp, dp]
+        L.ref_forward_field.restype = None
+        L.ref_adjoint.argtypes = [c_int, c_int, c_double, c_double, c_int, dp, dp, dp, c_int, ip, dp, dp]
+        L.ref_adjoint.restype = None
+        L.ref_hessian_ii.argtypes = [c_int, c_int, c_double, c_double, c_int, dp, dp, dp, c_int, ip,
+                                     dp, dp, c_double, dp, dp]
+        L.ref_hessian_ii.restype = c_int
         _lib = L
     return _lib
 
@@ -223,6 +238,60 @@ def scaled_logdet(H):
     Ht = np.zeros(49)
     rc = lib().ref_scaled_logdet(_pd(Hd), ctypes.byref(ld), _pd(Ht))
     return ld.value, Ht.reshape(7, 7), rc == 0
+
+
+def delta_weights_dxs2(alpha: float, h: float):
+    """Second x_s-derivatives of the delta and delta' weights (Alg. 1 step 9)."""
+    d = np.zeros(6)
+    dp = np.zeros(6)
+    lib().ref_delta_1d_dxs2(float(alpha), float(h), _pd(d), _pd(dp))
+    return d, dp
+
+
+def stf_derivs(t: float, ts: float, ws: float):
+    """(S, S_ts, S_w, S_tsts, S_tsw, S_ww) at t."""
+    out = np.zeros(6)
+    lib().ref_stf_derivs(float(t), float(ts), float(ws), _pd(out))
+    return out
+
+
+def jacobian_sensitivity(grid: Grid, theta):
+    """J[j][m][r][c] = dg/dtheta_j from sensitivity solves (Alg. 1 steps 1-3)."""
+    J = np.zeros((7, grid.nsteps + 1, grid.nrec, 2))
+    rc = lib().ref_jacobian_sens(*grid._args(), _pd(_d(theta)), _pd(J))
+    if rc != 0:
+        raise ValueError("source patch leaves the grid interior")
+    return J
+
+
+def forward_field(grid: Grid, f):
+    """Seismograms of a full forcing sequence f[m][c][nz][nx], m < nsteps."""
+    f = _d(f)
+    assert f.shape == (grid.nsteps, 2, grid.nz, grid.nx)
+    g = np.zeros((grid.nsteps + 1, grid.nrec, 2))
+    lib().ref_forward_field(*grid._args(), _pd(f), _pd(g))
+    return g
+
+
+def adjoint(grid: Grid, w):
+    """Dual solve (Eq. Dual_problems): dJ/df^m [m][c][nz][nx] for J = sum w . g."""
+    w = _d(w)
+    assert w.shape == (grid.nsteps + 1, grid.nrec, 2)
+    gf = np.zeros((grid.nsteps, 2, grid.nz, grid.nx))
+    lib().ref_adjoint(*grid._args(), _pd(w), _pd(gf))
+    return gf
+
+
+def hessian_ii(grid: Grid, theta, y, sigma):
+    """(H_II [7][7], dL/dtheta [7]) at theta for data y (Alg. 1 steps 6-10)."""
+    y = _d(y)
+    assert y.shape == (grid.nsteps + 1, grid.nrec, 2)
+    H2 = np.zeros(49)
+    gr = np.zeros(7)
+    rc = lib().ref_hessian_ii(*grid._args(), _pd(_d(theta)), _pd(y), float(sigma), _pd(H2), _pd(gr))
+    if rc != 0:
+        raise ValueError("source patch leaves the grid interior")
+    return H2.reshape(7, 7), gr
 
 
 def scaled_logdet_sub(H, free):

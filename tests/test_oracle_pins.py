@@ -672,3 +672,125 @@ def test_dlmc_special_case_and_linear_gaussian_closed_form(oracle):
     assert 0.3 < exact < 2.0
     assert -4 * se < big - exact < 4 * se + 0.02
     assert small - exact > big - exact + 2 * se
+
+
+# ------------------------------------------------ H_II: dual solve (Alg. 1 steps 6-10)
+@pytest.mark.parametrize("alpha", [0.0, 0.23, 0.5, 0.91])
+def test_delta_second_derivative_weights(oracle, alpha):
+    """d2/dx_s2 of the delta / delta' weights: central differences of the first derivatives,
+    and the twice-differentiated moment conditions
+    h sum d''_j (x_j - x_s)^q - 2 q h sum d'_j (x_j - x_s)^(q-1) + q (q-1) h sum d_j (x_j - x_s)^(q-2) = 0
+    for delta (the moments are constants) and the same with q [q = 1] on the right for delta'
+    replaced by 0 after two derivatives."""
+    h = 7.0
+    d2, dp2 = oracle.delta_weights_dxs2(alpha, h)
+    e = 1e-6
+    a1, b1 = oracle.delta_weights_dxs(alpha + e, h)
+    a0, b0 = oracle.delta_weights_dxs(alpha - e, h)
+    assert np.allclose(d2, (a1 - a0) / (2 * e * h), rtol=1e-6, atol=1e-9 * np.abs(d2).max())
+    assert np.allclose(dp2, (b1 - b0) / (2 * e * h), rtol=1e-6, atol=1e-9 * np.abs(dp2).max())
+    d, dp = oracle.delta_weights(alpha, h)
+    d1, dp1 = oracle.delta_weights_dxs(alpha, h)
+    xj = (np.arange(-2, 4) - alpha) * h
+    for (w0, w1, w2) in ((d, d1, d2), (dp, dp1, dp2)):
+        for q in range(5):
+            t = h * np.sum(w2 * xj ** q)
+            if q >= 1:
+                t -= 2 * q * h * np.sum(w1 * xj ** (q - 1))
+            if q >= 2:
+                t += q * (q - 1) * h * np.sum(w0 * xj ** (q - 2))
+            assert abs(t) < 1e-8 * max(1.0, h ** q) / h ** 2
+
+
+def test_stf_derivatives_match_finite_differences(oracle):
+    t, ts, ws = 0.37, 0.21, 6.3
+    d = oracle.stf_derivs(t, ts, ws)
+    e = 1e-5
+    S = lambda a, b: oracle.stf(t, a, b)
+    assert abs(d[0] - S(ts, ws)) < 1e-15
+    assert abs(d[1] - (S(ts + e, ws) - S(ts - e, ws)) / (2 * e)) < 1e-7 * abs(d[1])
+    assert abs(d[2] - (S(ts, ws + e) - S(ts, ws - e)) / (2 * e)) < 1e-7 * max(1, abs(d[2]))
+    dd = lambda a, b: oracle.stf_derivs(t, a, b)
+    assert abs(d[3] - (dd(ts + e, ws)[1] - dd(ts - e, ws)[1]) / (2 * e)) < 1e-6 * abs(d[3])
+    assert abs(d[4] - (dd(ts, ws + e)[1] - dd(ts, ws - e)[1]) / (2 * e)) < 1e-6 * abs(d[4])
+    assert abs(d[5] - (dd(ts, ws + e)[2] - dd(ts, ws - e)[2]) / (2 * e)) < 1e-6 * max(1, abs(d[5]))
+
+
+@pytest.fixture(scope="module")
+def adj_setup(oracle):
+    w = W.tiny(nx=36, nz=19, h=50.0, nsteps=70, nrec=4,
+               layers=((0.0, 2000.0, 1155.0, 2200.0), (400.0, 3000.0, 1732.0, 2500.0)))
+    return w, oracle.Grid.from_workload(w)
+
+
+def test_adjoint_is_the_transpose_of_the_scheme(adj_setup, oracle):
+    """<w, G f> = <G^T w, f> for random forcing sequences and receiver weights (the dual
+    problem, Eq. Dual_problems, is the exact transpose of the discrete scheme, free surface,
+    layer interface and absorbing rows included)."""
+    w, G = adj_setup
+    rng = np.random.default_rng(8)
+    for _ in range(2):
+        f = rng.standard_normal((w.nsteps, 2, w.nz, w.nx))
+        wt = rng.standard_normal((w.nsteps + 1, w.nrec, 2))
+        lhs = float(np.sum(wt * oracle.forward_field(G, f)))
+        rhs = float(np.sum(oracle.adjoint(G, wt) * f))
+        assert abs(lhs - rhs) < 1e-11 * max(abs(lhs), 1.0)
+
+
+def _theta_adj(w):
+    return np.array([906.0, 431.0, 0.16, 6.4, 5e13, 3e13, 7e13])
+
+
+def test_cost_gradient_from_dual_solve_equals_jacobian_transpose(adj_setup, oracle):
+    """dL/dtheta = -J^T C^-1 r with J from the sensitivity solves (both exact derivatives of
+    the discrete scheme, so they agree to rounding); zero residual gives zero H_II and
+    gradient."""
+    w, G = adj_setup
+    th = _theta_adj(w)
+    g = oracle.forward(G, th)
+    rng = np.random.default_rng(2)
+    sigma = 0.4
+    y = g + sigma * rng.standard_normal(g.shape)
+    H2, grad = oracle.hessian_ii(G, th, y, sigma)
+    J = oracle.jacobian_sensitivity(G, th)
+    wt = (y - g) / sigma ** 2
+    ref = -np.array([np.sum(J[j] * wt) for j in range(7)])
+    scale = np.sqrt(np.sum(J.reshape(7, -1) ** 2, 1)) * np.sqrt(np.sum(wt ** 2))
+    assert np.all(np.abs(grad - ref) <= 1e-10 * scale)
+    assert np.allclose(H2, H2.T, rtol=0, atol=0)
+    H0, g0 = oracle.hessian_ii(G, th, g, sigma)
+    assert np.all(H0 == 0.0) and np.all(g0 == 0.0)
+
+
+def test_hessian_ii_equals_curvature_of_the_seismograms(adj_setup, oracle):
+    """H_II = -sum w . d2 g / dtheta_a dtheta_b (Thm 2's H_2) against central differences of
+    the sensitivity Jacobian: O(d^2), four times smaller at half the step, in every entry
+    scaled by sqrt(|H_aa H_bb|) of the Gauss-Newton part."""
+    w, G = adj_setup
+    th = _theta_adj(w)
+    g = oracle.forward(G, th)
+    rng = np.random.default_rng(4)
+    sigma = 0.4
+    y = g + sigma * rng.standard_normal(g.shape)
+    H2, _ = oracle.hessian_ii(G, th, y, sigma)
+    wt = (y - g) / sigma ** 2
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+
+    def fd(rel):
+        out = np.zeros((7, 7))
+        for b in range(7):
+            d = rel * (hi[b] - lo[b])
+            tp, tm = th.copy(), th.copy()
+            tp[b] += d
+            tm[b] -= d
+            Jp, Jm = oracle.jacobian_sensitivity(G, tp), oracle.jacobian_sensitivity(G, tm)
+            for a in range(7):
+                out[a, b] = -np.sum((Jp[a] - Jm[a]) * wt) / (2 * d)
+        return out
+
+    H1 = oracle.node_hessian_sensitivity(G, th, sigma)
+    sc = np.sqrt(np.outer(np.diag(H1), np.diag(H1)))
+    e1 = np.max(np.abs(fd(2e-3) - H2) / sc)
+    e2 = np.max(np.abs(fd(1e-3) - H2) / sc)
+    assert e1 < 1e-4 and e2 < e1 / 3.0
+    assert np.max(np.abs(H2) / sc) > 1e-3   # the check is not vacuous
