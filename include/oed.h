@@ -216,6 +216,48 @@ int oed_eig_subset(oed_ctx *ctx, const double *H, int n, const double *w, const 
                    const double *hi, int param_mask, double *eig, double *dkl, int *status,
                    int *n_bad, void *stream);
 
+/* Second part of the Hessian of the cost L = 1/2 sum_m sum_r r^T C^-1 r,
+ * r = y - g(theta), C = sigma^2 I, from one primal and one dual solve per node
+ * (Alg. 1 steps 6-10; Eq. H2_numerics; Thm 2's H_2):
+ *   step 6-7:  primal solve at theta, w = C^-1 (y - g(theta)) at the receivers,
+ *   step 8:    dual problem (Eq. Dual_problems), the transpose of the scheme run
+ *              backwards from w: lambda = dJ/d(forcing) for J = sum w . g,
+ *   step 9-10: H_II = -sum lambda . d2f/dtheta2 with the analytic second
+ *              derivatives of the discrete source (delta weights in x_s, z_s;
+ *              S(t) in t_s, omega_s; d2f/dm dm = 0).
+ * H_II is ADDED to H (pass H_1 from oed_hessian to get H_1 + H_II, Eq.
+ * Hessian_Y with a uniform prior); grad receives dL/dtheta = -J^T C^-1 r.
+ *   theta   device [n][7]
+ *   y       device [n][nsteps+1][nrec][2] FP64 data (e.g. g(theta*) + eps)
+ *   H       device [n][7][7] in/out
+ *   grad    device [n][7] or NULL
+ *   status  device [n] or NULL: 0, or OED_EINVAL if the source leaves the
+ *           interior (H and grad of that node become NaN)
+ * nrec <= 256.  The first call on a context allocates FP64 scratch for
+ * max_solves nodes (cudaMalloc; OED_ENOMEM if it fails).  Asynchronous on
+ * `stream` apart from that first allocation. */
+int oed_hessian_ii(oed_ctx *ctx, const double *theta, int n, const double *y, double sigma, double *H,
+                   double *grad, int *status, void *stream);
+
+/* One Newton step per node toward the minimiser of the cost (Thm 1): solve
+ * H d = -grad with the scaled Cholesky of H, theta += d, clamped to the prior box
+ * [lo, hi].  A node whose H is not positive definite keeps its theta (status
+ * OED_ENOTPD).  H [n][7][7], grad [n][7], theta [n][7] (in/out), status [n] or
+ * NULL, all device; lo, hi host [7].  Synchronises `stream`. */
+int oed_newton_step(const double *H, const double *grad, int n, const double *lo, const double *hi, double *theta,
+                    int *status, void *stream);
+
+/* The estimate theta-hat of Thm 1 and the Hessian of Thm 2 at it, for Thm 3's
+ * refined gain: starting from theta (device [n][7], in/out), `iters` Newton steps
+ * on the cost with H = H_1 + H_II (H_1 from oed_hessian in the context's Jacobian
+ * form, H_II from oed_hessian_ii), then H (device [n][7][7]) = H_1 + H_II and grad
+ * (device [n][7]) at the final theta.  Thm 3's per-node gain is then
+ * 1/2 log det H - 7/2 (1 + log 2 pi) - h, which oed_eig computes from H.
+ * iters in 0..100 (0: H_1 + H_II at the given theta). */
+int oed_hessian_map(oed_ctx *ctx, double *theta, int n, const double *y, const double *lo, const double *hi,
+                    double rel_step, double sigma, int iters, double *H, double *grad, int *status,
+                    void *stream);
+
 /* Double-loop (nested) Monte Carlo estimate of the expected information gain:
  * Eq. expected_I sampled directly, the estimator the Laplace method replaces
  * (Sec. 4.4 compares the two).  With y_n = g_outer[n] + eps[n] and noise sigma^2 I,

@@ -31,7 +31,8 @@ SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_resident_min_cluster", "oed_set_jacobian", "oed_get_jacobian",
            "oed_gauss_newton_noalloc", "oed_server_create", "oed_server_request_bytes",
            "oed_server_submit", "oed_server_poll", "oed_server_wait", "oed_server_stats",
-           "oed_server_destroy", "oed_eig_subset", "oed_dlmc")
+           "oed_server_destroy", "oed_eig_subset", "oed_dlmc", "oed_hessian_ii", "oed_newton_step",
+           "oed_hessian_map")
 
 
 class OedError(RuntimeError):
@@ -89,6 +90,9 @@ def library():
         "oed_eig_designs": (i, [vp, vp, i, i, i, i, vp, i, vp, dp, dp, vp, vp, vp]),
         "oed_eig_subset": (i, [vp, vp, i, vp, dp, dp, i, vp, vp, vp, vp, vp]),
         "oed_dlmc": (i, [vp, vp, i, vp, i, i, d, vp, vp, vp]),
+        "oed_hessian_ii": (i, [vp, vp, i, vp, d, vp, vp, vp, vp]),
+        "oed_newton_step": (i, [vp, vp, i, dp, dp, vp, vp, vp]),
+        "oed_hessian_map": (i, [vp, vp, i, vp, dp, dp, d, d, i, vp, vp, vp, vp]),
         "oed_nodes_mc": (i, [vp, i, dp, dp, vp, vp, vp]),
         "oed_nodes_smolyak": (i, [i, i, dp, dp, i, dp, dp, ip]),
         "oed_eig_host": (i, [vp, dp, dp, i, dp, dp, d, d, dp, dp, ip]),
@@ -296,6 +300,30 @@ def oed_eig_subset(ctx: Optional[Context], H, w, lo, hi, free, eig, dkl=None, st
                                   _ptr(dkl), _ptr(status), _ptr(n_bad), _stream(stream))
     _check(h, rc, "oed_eig_subset")
     return eig
+
+
+def oed_hessian_ii(ctx: Context, theta, y, sigma: float, H, grad=None, status=None, stream=None):
+    """Adds H_II (Alg. 1 steps 6-10) at theta for data y to H; dL/dtheta into grad."""
+    n = theta.shape[0]
+    _check(ctx.handle, library().oed_hessian_ii(ctx.handle, _ptr(theta), n, _ptr(y), float(sigma), _ptr(H),
+                                                _ptr(grad), _ptr(status), _stream(stream)), "oed_hessian_ii")
+    return H
+
+
+def oed_newton_step(H, grad, theta, lo, hi, status=None, stream=None):
+    """theta += -H^-1 grad per node, clamped to [lo, hi] (device tensors)."""
+    _check(None, library().oed_newton_step(_ptr(H), _ptr(grad), theta.shape[0], _darr(lo), _darr(hi),
+                                           _ptr(theta), _ptr(status), _stream(stream)), "oed_newton_step")
+    return theta
+
+
+def oed_hessian_map(ctx: Context, theta, y, lo, hi, rel_step: float, sigma: float, iters: int, H, grad,
+                    status=None, stream=None):
+    """Newton iterations to the estimate of Thm 1; H = H_1 + H_II and grad at it."""
+    _check(ctx.handle, library().oed_hessian_map(ctx.handle, _ptr(theta), theta.shape[0], _ptr(y), _darr(lo),
+                                                 _darr(hi), float(rel_step), float(sigma), int(iters), _ptr(H),
+                                                 _ptr(grad), _ptr(status), _stream(stream)), "oed_hessian_map")
+    return H
 
 
 def oed_dlmc(g_outer, eps, g_inner, sigma, log_ev, eig=None, stream=None):

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liboed.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "source.cu", "stencil.cu", "stream_tma.cu", "resident.cu", "hessian.cu", "logdet.cu", "dlmc.cu",
+SOURCES = ["api.cu", "source.cu", "stencil.cu", "stream_tma.cu", "resident.cu", "hessian.cu", "logdet.cu", "dlmc.cu", "adjoint.cu",
            "noalloc.cu", "smolyak.cpp", "server.cpp"]
 HEADERS = [os.path.join(CSRC, "oed_internal.cuh"), os.path.join(CSRC, "stencil_cell.cuh"),
            os.path.join(ROOT, "include", "oed.h")]

@@ -262,6 +262,7 @@ int oed_destroy(oed_ctx *ctx)
     cudaFree(ctx->h_stage_dkl);
     cudaFree(ctx->h_stage_eig);
     cudaFree(ctx->h_stage_bad);
+    cudaFree(ctx->d_adj);
     delete ctx;
     return OED_OK;
 }
@@ -482,6 +483,81 @@ int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, cons
                        status ? status + off : nullptr, st);
     }
     return cuda_err(ctx, cudaGetLastError(), "oed_hessian");
+}
+
+int oed_hessian_ii(oed_ctx *ctx, const double *theta, int n, const double *y, double sigma, double *H,
+                   double *grad, int *status, void *stream)
+{
+    if (!ctx) return OED_EINVAL;
+    if (n < 0 || (n > 0 && (!theta || !y || !H)))
+        return set_err(ctx, OED_EINVAL, "oed_hessian_ii: bad pointer arguments");
+    if (!(sigma > 0) || !std::isfinite(sigma)) return set_err(ctx, OED_EINVAL, "oed_hessian_ii: sigma must be positive");
+    if (ctx->g.nrec > kMaxRecHessian) return set_err(ctx, OED_EINVAL, "oed_hessian_ii: at most 256 receivers");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t per = (size_t)ctx->g.nlev * ctx->g.nrec * 2;
+    const int chunk = ctx->max_solves;
+    const size_t need = ((size_t)chunk * per + (size_t)chunk * 6 * 2 * kPatch * kPatch) * sizeof(double);
+    if (ctx->adj_bytes < need) {
+        cudaStreamSynchronize(st);
+        cudaFree(ctx->d_adj);
+        ctx->d_adj = nullptr;
+        ctx->adj_bytes = 0;
+        if (cudaMalloc((void **)&ctx->d_adj, need) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, OED_ENOMEM, "oed_hessian_ii: no device memory for the dual solve");
+        }
+        ctx->adj_bytes = need;
+    }
+    double *w = ctx->d_adj, *acc = ctx->d_adj + (size_t)chunk * per;
+    for (int off = 0; off < n; off += chunk) {
+        const int nb = std::min(chunk, n - off);
+        launch_sources(ctx, theta + (size_t)off * kNT, nb, 1, nullptr, st);   // step 6: primal
+        int rc = run_steps(ctx, nb, st);
+        if (rc) return rc;
+        launch_adjoint(ctx, nb, y + (size_t)off * per, sigma, w, acc, st);     // steps 7-8: dual
+        launch_hii_combine(ctx, nb, acc, H + (size_t)off * 49, grad ? grad + (size_t)off * kNT : nullptr,
+                           status ? status + off : nullptr, st);              // steps 9-10
+    }
+    return cuda_err(ctx, cudaGetLastError(), "oed_hessian_ii");
+}
+
+int oed_newton_step(const double *H, const double *grad, int n, const double *lo, const double *hi, double *theta,
+                    int *status, void *stream)
+{
+    if (n < 0 || (n > 0 && (!H || !grad || !theta)) || !lo || !hi) return OED_EINVAL;
+    double lh[2 * kNT];
+    for (int j = 0; j < kNT; j++) {
+        if (!(hi[j] > lo[j])) return OED_EINVAL;
+        lh[j] = lo[j];
+        lh[kNT + j] = hi[j];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double *d_lh = nullptr;
+    if (cudaMallocAsync((void **)&d_lh, sizeof(lh), st) != cudaSuccess) return OED_ENOMEM;
+    cudaMemcpyAsync(d_lh, lh, sizeof(lh), cudaMemcpyHostToDevice, st);
+    launch_newton(H, grad, n, d_lh, theta, status, st);
+    cudaFreeAsync(d_lh, st);
+    const cudaError_t e = cudaStreamSynchronize(st);   // the host array lh must outlive the copy
+    return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? OED_OK : OED_ECUDA;
+}
+
+int oed_hessian_map(oed_ctx *ctx, double *theta, int n, const double *y, const double *lo, const double *hi,
+                    double rel_step, double sigma, int iters, double *H, double *grad, int *status,
+                    void *stream)
+{
+    if (!ctx) return OED_EINVAL;
+    if (iters < 0 || iters > 100) return set_err(ctx, OED_EINVAL, "oed_hessian_map: iters must be in 0..100");
+    if (n < 0 || (n > 0 && (!theta || !y || !H || !grad))) return set_err(ctx, OED_EINVAL, "oed_hessian_map: bad pointers");
+    for (int it = 0; it <= iters; it++) {
+        int rc = oed_hessian(ctx, theta, n, lo, hi, rel_step, sigma, nullptr, 0, H, nullptr, status, stream);
+        if (rc) return rc;
+        rc = oed_hessian_ii(ctx, theta, n, y, sigma, H, grad, status, stream);
+        if (rc) return rc;
+        if (it == iters) break;
+        rc = oed_newton_step(H, grad, n, lo, hi, theta, nullptr, stream);
+        if (rc) return set_err(ctx, rc, "oed_hessian_map: Newton step");
+    }
+    return OED_OK;
 }
 
 static double log_volume(const double *lo, const double *hi)

@@ -186,6 +186,62 @@ __global__ void __launch_bounds__(256) k_designs(const double *__restrict__ H_re
     }
 }
 
+// One Newton step per node on the cost L (Thm 1's estimator): solve H d = -grad with
+// the scaled Cholesky of H (S^-1 H S^-1 = L L^T), theta += d, clamped to the prior
+// box.  A node whose H is not positive definite keeps its theta (status OED_ENOTPD).
+__global__ void k_newton(const double *__restrict__ H, const double *__restrict__ grad, int n,
+                         const double *__restrict__ lohi, double *__restrict__ theta, int *__restrict__ status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *h = H + (size_t)i * 49;
+    double S[kNT], L[kNT][kNT], y[kNT];
+    int bad = 0;
+    for (int a = 0; a < kNT; a++) {
+        const double d = h[a * kNT + a];
+        bad |= !(d > 0.0) || !isfinite(d);
+        S[a] = bad ? 1.0 : sqrt(d);
+    }
+    for (int j = 0; j < kNT && !bad; j++) {
+        double s = h[j * kNT + j] / (S[j] * S[j]);
+        for (int k = 0; k < j; k++) s -= L[j][k] * L[j][k];
+        if (!(s > 0.0) || !isfinite(s)) {
+            bad = 1;
+            break;
+        }
+        L[j][j] = sqrt(s);
+        for (int r = j + 1; r < kNT; r++) {
+            double t = h[r * kNT + j] / (S[r] * S[j]);
+            for (int k = 0; k < j; k++) t -= L[r][k] * L[j][k];
+            L[r][j] = t / L[j][j];
+        }
+    }
+    if (!bad) {
+        // (S L L^T S) d = -grad:  L z = -S^-1 grad, L^T e = z, d = S^-1 e
+        for (int a = 0; a < kNT; a++) {
+            double t = -grad[(size_t)i * kNT + a] / S[a];
+            for (int k = 0; k < a; k++) t -= L[a][k] * y[k];
+            y[a] = t / L[a][a];
+        }
+        for (int a = kNT - 1; a >= 0; a--) {
+            double t = y[a];
+            for (int k = a + 1; k < kNT; k++) t -= L[k][a] * y[k];
+            y[a] = t / L[a][a];
+        }
+        for (int a = 0; a < kNT; a++) {
+            const double v = theta[(size_t)i * kNT + a] + y[a] / S[a];
+            theta[(size_t)i * kNT + a] = fmin(fmax(v, lohi[a]), lohi[kNT + a]);
+        }
+    }
+    if (status) status[i] = bad ? OED_ENOTPD : 0;
+}
+
+void launch_newton(const double *H, const double *grad, int n, const double *lohi, double *theta, int *status,
+                   cudaStream_t s)
+{
+    if (n > 0) k_newton<<<(n + 127) / 128, 128, 0, s>>>(H, grad, n, lohi, theta, status);
+}
+
 struct LoHi {
     double v[2 * kNT];
 };

@@ -127,6 +127,8 @@ struct oed_ctx {
     std::map<int, cudaGraphExec_t> graphs;   // nsolve -> captured time loop
     cudaEvent_t ev_steps[2] = {nullptr, nullptr};   // recorded around the stencil launches
     int last_steps_launches = 0;
+    double *d_adj = nullptr;        // oed_hessian_ii: residual weights, then patch sums
+    size_t adj_bytes = 0;
     std::string err;
 };
 
@@ -163,6 +165,14 @@ int resident_max_active_clusters(const oed_ctx *ctx, int C);
 cudaError_t launch_resident(const oed_ctx *ctx, int C, int nsolve, cudaStream_t st, cudaEvent_t ev0,
                             cudaEvent_t ev1, int nsteps_override);
 
+// adjoint.cu: residual weights w = (y - g)/sigma^2 from the primal traces, then the
+// dual solve into the patch time sums acc[nsolve][6][2][49]
+void launch_adjoint(const oed_ctx *ctx, int nsolve, const double *y, double sigma, double *w, double *acc,
+                    cudaStream_t st);
+// source.cu: gradient and H_II (added to H) from those sums
+void launch_hii_combine(const oed_ctx *ctx, int nsolve, const double *acc, double *H, double *grad, int *status,
+                        cudaStream_t st);
+
 // hessian.cu
 void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double sigma,
                     const int *seg_end, int nseg, const int *win_seg, int nwin, double *H,
@@ -174,6 +184,8 @@ void launch_eig(const double *H, int n, const double *w, double logvol, int pmas
 void launch_eig_designs(const double *H_rec, int n, int nrec, int nwin, int win,
                         const unsigned char *mask, int ndesign, const double *w, double logvol,
                         double *eig, int *n_bad, cudaStream_t s);
+void launch_newton(const double *H, const double *grad, int n, const double *lohi, double *theta, int *status,
+                   cudaStream_t s);
 void launch_nodes_mc(const double *u, int M, const double *lo, const double *hi, double *theta,
                      double *w, cudaStream_t s);
 

@@ -56,6 +56,28 @@ __device__ void delta_weights_dxs(double a, double h, double *d, double *dp)
     dp[5] = (-5.0 / 2.0 * a * a - Rp) * ih3;
 }
 
+// d2/dx_s2 of the six delta and delta' weights (the forcing's second derivatives,
+// Alg. 1 step 9; the regularised delta is C^2 in x_s): (1/h^2) d2/dalpha2 of the
+// printed polynomials.
+__device__ void delta_weights_dxs2(double a, double h, double *d, double *dp)
+{
+    const double Ppp = a * a * a * (100.0 / 3.0 + a * (-35.0 / 4.0 + a * (-119.0 / 2.0 + a * (63.0 - 18.0 * a))));
+    const double Rpp = a * a * (-25.0 + a * (-15.0 + a * (295.0 / 2.0 + a * (-168.0 + 56.0 * a))));
+    const double h3 = h * h * h, h4 = h3 * h;
+    d[0] = (-1.0 / 12.0 + a * (-1.0 / 2.0 - 19.0 / 2.0 * a) + Ppp) / h3;
+    d[1] = (4.0 / 3.0 + a * (1.0 + 48.0 * a) - 5.0 * Ppp) / h3;
+    d[2] = (-5.0 / 2.0 - 97.0 * a * a + 10.0 * Ppp) / h3;
+    d[3] = (4.0 / 3.0 + a * (-1.0 + 98.0 * a) - 10.0 * Ppp) / h3;
+    d[4] = (-1.0 / 12.0 + a * (1.0 / 2.0 - 99.0 / 2.0 * a) + 5.0 * Ppp) / h3;
+    d[5] = (10.0 * a * a - Ppp) / h3;
+    dp[0] = (1.0 / 2.0 + 4.0 * a + Rpp) / h4;
+    dp[1] = (-1.0 - 21.0 * a - 5.0 * Rpp) / h4;
+    dp[2] = (44.0 * a + 10.0 * Rpp) / h4;
+    dp[3] = (1.0 - 46.0 * a - 10.0 * Rpp) / h4;
+    dp[4] = (-1.0 / 2.0 + 24.0 * a + 5.0 * Rpp) / h4;
+    dp[5] = (-5.0 * a - Rpp) / h4;
+}
+
 struct FdStep {
     double d[kNT];
 };
@@ -330,6 +352,114 @@ void launch_rows(oed_ctx *ctx, cudaStream_t s)
                                           (FacCoef<float> *)ctx->d_fac);
     cudaFreeAsync(d_lay, s);
     cudaStreamSynchronize(s);   // the host vector `lay` must outlive the copy
+}
+
+// Cost gradient and H_II from the dual solve (Alg. 1 steps 9-10, Eq. H2_numerics).
+// The forcing of a solve is S(t) W on the 6x6 patch, W = dt^2/nu_row P(x_s, z_s, M),
+//   P_x = m_xx d'(x) d(z) + m_xz d(x) d'(z),   P_z = m_xz d'(x) d(z) + m_zz d(x) d'(z),
+// with d, d' the delta / delta' weights.  acc[t][c][node] = sum_m lambda^{m+1} S_t(t_m)
+// (t = S, S_ts, S_w, S_tsts, S_tsw, S_ww), so with dJ/d(S W)^m = lambda^{m+1}
+//   d2J/dth_p dth_q = sum_c sum_node acc[time part of (p,q)] * d^k W / (space part of (p,q))
+// where t_s, omega_s differentiate S, x_s and z_s the weights of their axis, m_k
+// select their moment term (d2/dm dm = 0).  H_II = -d2J (added to H), grad = -dJ.
+// One block per solve; thread t < 28 takes the upper-triangle pair t, 28 <= t < 35
+// the gradient entry t - 28.
+template <typename real>
+__global__ void __launch_bounds__(64) k_hii_combine(const double *__restrict__ theta, const double *__restrict__ acc,
+                                                    const SourceDesc<real> *__restrict__ src,
+                                                    const RowCoef<real> *__restrict__ rows, Geometry g,
+                                                    double *__restrict__ H, double *__restrict__ grad,
+                                                    int *__restrict__ status)
+{
+    const int s = blockIdx.x, t = threadIdx.x;
+    const double *th = theta + (size_t)s * kNT;
+    __shared__ double W[2][3][2][6];   // axis, derivative order, delta / delta', node
+    __shared__ double rf[6];
+    const bool ok = src[s].ok;
+    if (t == 0 && ok) {
+        for (int axis = 0; axis < 2; axis++) {
+            const double q = th[axis] / g.h, al = q - floor(q);
+            delta_weights(al, g.h, W[axis][0][0], W[axis][0][1]);
+            delta_weights_dxs(al, g.h, W[axis][1][0], W[axis][1][1]);
+            delta_weights_dxs2(al, g.h, W[axis][2][0], W[axis][2][1]);
+        }
+        for (int b = 0; b < 6; b++) rf[b] = (double)rows[src[s].j0 + b].rf;
+    }
+    __syncthreads();
+    if (t >= 35) return;
+    int p, q;
+    if (t < 28) {   // upper-triangle pair number t
+        p = 0;
+        int r = t;
+        while (r >= kNT - p) {
+            r -= kNT - p;
+            p++;
+        }
+        q = p + r;
+    } else {
+        p = t - 28;
+        q = -1;
+    }
+    if (!ok) {
+        if (t < 28) {
+            H[(size_t)s * 49 + p * kNT + q] = NAN;
+            H[(size_t)s * 49 + q * kNT + p] = NAN;
+        } else if (grad) {
+            grad[(size_t)s * kNT + p] = NAN;
+        }
+        if (t == 0 && status) status[s] = OED_EINVAL;
+        return;
+    }
+    // derivative orders of the two axes, the time part and the moment selection
+    const int ordx = (p == 0) + (q == 0), ordz = (p == 1) + (q == 1);
+    const int nt = (p == 2 || p == 3) + (q == 2 || q == 3);
+    const int nm = (p >= 4) + (q >= 4);
+    double v = 0.0;
+    if (nm < 2) {
+        int tk;   // S-derivative index of acc
+        if (nt == 0)
+            tk = 0;
+        else if (nt == 1)
+            tk = (p == 2 || q == 2) ? 1 : 2;
+        else
+            tk = (p == 2 && q == 2) ? 3 : ((p == 3 && q == 3) ? 5 : 4);
+        const double *ac = acc + (size_t)s * 6 * 2 * kPatch * kPatch + (size_t)tk * 2 * kPatch * kPatch;
+        // moment terms of each component: (moment index, kind of the x factor; z factor the other)
+        const int tm[2][2] = {{4, 5}, {5, 6}};
+        const int xk[2][2] = {{1, 0}, {1, 0}};
+        for (int c = 0; c < 2; c++)
+            for (int b = 0; b < 6; b++)
+                for (int a = 0; a < 6; a++) {
+                    double P = 0.0;
+                    for (int k = 0; k < 2; k++) {
+                        const int mk = tm[c][k];
+                        double coef = th[mk];
+                        if (nm == 1) coef = (p == mk || q == mk) ? 1.0 : 0.0;
+                        P += coef * W[0][ordx][xk[c][k]][a] * W[1][ordz][1 - xk[c][k]][b];
+                    }
+                    v += ac[c * kPatch * kPatch + b * kPatch + a] * rf[b] * P;
+                }
+    }
+    if (t < 28) {
+        H[(size_t)s * 49 + p * kNT + q] -= v;
+        if (q != p) H[(size_t)s * 49 + q * kNT + p] -= v;
+    } else if (grad) {
+        grad[(size_t)s * kNT + p] = -v;
+    }
+    if (t == 0 && status) status[s] = 0;
+}
+
+void launch_hii_combine(const oed_ctx *ctx, int nsolve, const double *acc, double *H, double *grad, int *status,
+                        cudaStream_t st)
+{
+    if (nsolve <= 0) return;
+    if (ctx->precision == OED_FP64)
+        k_hii_combine<double><<<nsolve, 64, 0, st>>>(ctx->d_theta, acc, (const SourceDesc<double> *)ctx->d_src,
+                                                     (const RowCoef<double> *)ctx->d_rows, ctx->g, H, grad,
+                                                     status);
+    else
+        k_hii_combine<float><<<nsolve, 64, 0, st>>>(ctx->d_theta, acc, (const SourceDesc<float> *)ctx->d_src,
+                                                    (const RowCoef<float> *)ctx->d_rows, ctx->g, H, grad, status);
 }
 
 void launch_sources(const oed_ctx *ctx, const double *theta_nodes, int nnode, int per_node,
