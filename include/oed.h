@@ -239,24 +239,28 @@ int oed_eig_subset(oed_ctx *ctx, const double *H, int n, const double *w, const 
 int oed_hessian_ii(oed_ctx *ctx, const double *theta, int n, const double *y, double sigma, double *H,
                    double *grad, int *status, void *stream);
 
-/* One Newton step per node toward the minimiser of the cost (Thm 1): solve
- * H d = -grad with the scaled Cholesky of H, theta += d, clamped to the prior box
- * [lo, hi].  A node whose H is not positive definite keeps its theta (status
- * OED_ENOTPD).  H [n][7][7], grad [n][7], theta [n][7] (in/out), status [n] or
- * NULL, all device; lo, hi host [7].  Synchronises `stream`. */
-int oed_newton_step(const double *H, const double *grad, int n, const double *lo, const double *hi, double *theta,
-                    int *status, void *stream);
+/* One Newton step per node toward the minimiser of the cost (Thm 1) over the
+ * unknown parameters (bit j of param_mask, 1..127; the others are known and
+ * stay put): solve H_FF d = -grad_F with the scaled Cholesky of H_FF,
+ * theta_F += d, clamped to the prior box [lo, hi].  A node whose H_FF is not
+ * positive definite keeps its theta (status OED_ENOTPD).  H [n][7][7],
+ * grad [n][7], theta [n][7] (in/out), status [n] or NULL, all device; lo, hi
+ * host [7].  Synchronises `stream`. */
+int oed_newton_step(const double *H, const double *grad, int n, const double *lo, const double *hi, int param_mask,
+                    double *theta, int *status, void *stream);
 
 /* The estimate theta-hat of Thm 1 and the Hessian of Thm 2 at it, for Thm 3's
  * refined gain: starting from theta (device [n][7], in/out), `iters` Newton steps
- * on the cost with H = H_1 + H_II (H_1 from oed_hessian in the context's Jacobian
+ * over the unknown parameters of param_mask (as oed_newton_step) on the cost with
+ * H = H_1 + H_II (H_1 from oed_hessian in the context's Jacobian
  * form, H_II from oed_hessian_ii), then H (device [n][7][7]) = H_1 + H_II and grad
  * (device [n][7]) at the final theta.  Thm 3's per-node gain is then
- * 1/2 log det H - 7/2 (1 + log 2 pi) - h, which oed_eig computes from H.
+ * 1/2 log det H - 7/2 (1 + log 2 pi) - h, which oed_eig (oed_eig_subset for a
+ * subset) computes from H.
  * iters in 0..100 (0: H_1 + H_II at the given theta). */
 int oed_hessian_map(oed_ctx *ctx, double *theta, int n, const double *y, const double *lo, const double *hi,
-                    double rel_step, double sigma, int iters, double *H, double *grad, int *status,
-                    void *stream);
+                    double rel_step, double sigma, int param_mask, int iters, double *H, double *grad,
+                    int *status, void *stream);
 
 /* Double-loop (nested) Monte Carlo estimate of the expected information gain:
  * Eq. expected_I sampled directly, the estimator the Laplace method replaces

@@ -91,8 +91,8 @@ def library():
         "oed_eig_subset": (i, [vp, vp, i, vp, dp, dp, i, vp, vp, vp, vp, vp]),
         "oed_dlmc": (i, [vp, vp, i, vp, i, i, d, vp, vp, vp]),
         "oed_hessian_ii": (i, [vp, vp, i, vp, d, vp, vp, vp, vp]),
-        "oed_newton_step": (i, [vp, vp, i, dp, dp, vp, vp, vp]),
-        "oed_hessian_map": (i, [vp, vp, i, vp, dp, dp, d, d, i, vp, vp, vp, vp]),
+        "oed_newton_step": (i, [vp, vp, i, dp, dp, i, vp, vp, vp]),
+        "oed_hessian_map": (i, [vp, vp, i, vp, dp, dp, d, d, i, i, vp, vp, vp, vp]),
         "oed_nodes_mc": (i, [vp, i, dp, dp, vp, vp, vp]),
         "oed_nodes_smolyak": (i, [i, i, dp, dp, i, dp, dp, ip]),
         "oed_eig_host": (i, [vp, dp, dp, i, dp, dp, d, d, dp, dp, ip]),
@@ -310,19 +310,28 @@ def oed_hessian_ii(ctx: Context, theta, y, sigma: float, H, grad=None, status=No
     return H
 
 
-def oed_newton_step(H, grad, theta, lo, hi, status=None, stream=None):
-    """theta += -H^-1 grad per node, clamped to [lo, hi] (device tensors)."""
-    _check(None, library().oed_newton_step(_ptr(H), _ptr(grad), theta.shape[0], _darr(lo), _darr(hi),
+def _mask(free):
+    m = 0
+    for j in free:
+        m |= 1 << int(j)
+    return m
+
+
+def oed_newton_step(H, grad, theta, lo, hi, free=range(7), status=None, stream=None):
+    """theta_F += -H_FF^-1 grad_F per node over the unknowns F, clamped to [lo, hi]."""
+    _check(None, library().oed_newton_step(_ptr(H), _ptr(grad), theta.shape[0], _darr(lo), _darr(hi), _mask(free),
                                            _ptr(theta), _ptr(status), _stream(stream)), "oed_newton_step")
     return theta
 
 
 def oed_hessian_map(ctx: Context, theta, y, lo, hi, rel_step: float, sigma: float, iters: int, H, grad,
-                    status=None, stream=None):
-    """Newton iterations to the estimate of Thm 1; H = H_1 + H_II and grad at it."""
+                    free=range(7), status=None, stream=None):
+    """Newton iterations over the unknowns F to the estimate of Thm 1; H = H_1 + H_II and
+    grad at it."""
     _check(ctx.handle, library().oed_hessian_map(ctx.handle, _ptr(theta), theta.shape[0], _ptr(y), _darr(lo),
-                                                 _darr(hi), float(rel_step), float(sigma), int(iters), _ptr(H),
-                                                 _ptr(grad), _ptr(status), _stream(stream)), "oed_hessian_map")
+                                                 _darr(hi), float(rel_step), float(sigma), _mask(free), int(iters),
+                                                 _ptr(H), _ptr(grad), _ptr(status), _stream(stream)),
+           "oed_hessian_map")
     return H
 
 

@@ -521,10 +521,11 @@ int oed_hessian_ii(oed_ctx *ctx, const double *theta, int n, const double *y, do
     return cuda_err(ctx, cudaGetLastError(), "oed_hessian_ii");
 }
 
-int oed_newton_step(const double *H, const double *grad, int n, const double *lo, const double *hi, double *theta,
-                    int *status, void *stream)
+int oed_newton_step(const double *H, const double *grad, int n, const double *lo, const double *hi, int param_mask,
+                    double *theta, int *status, void *stream)
 {
     if (n < 0 || (n > 0 && (!H || !grad || !theta)) || !lo || !hi) return OED_EINVAL;
+    if (param_mask < 1 || param_mask > 127) return OED_EINVAL;
     double lh[2 * kNT];
     for (int j = 0; j < kNT; j++) {
         if (!(hi[j] > lo[j])) return OED_EINVAL;
@@ -535,16 +536,18 @@ int oed_newton_step(const double *H, const double *grad, int n, const double *lo
     double *d_lh = nullptr;
     if (cudaMallocAsync((void **)&d_lh, sizeof(lh), st) != cudaSuccess) return OED_ENOMEM;
     cudaMemcpyAsync(d_lh, lh, sizeof(lh), cudaMemcpyHostToDevice, st);
-    launch_newton(H, grad, n, d_lh, theta, status, st);
+    launch_newton(H, grad, n, param_mask, d_lh, theta, status, st);
     cudaFreeAsync(d_lh, st);
     const cudaError_t e = cudaStreamSynchronize(st);   // the host array lh must outlive the copy
     return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? OED_OK : OED_ECUDA;
 }
 
 int oed_hessian_map(oed_ctx *ctx, double *theta, int n, const double *y, const double *lo, const double *hi,
-                    double rel_step, double sigma, int iters, double *H, double *grad, int *status,
-                    void *stream)
+                    double rel_step, double sigma, int param_mask, int iters, double *H, double *grad,
+                    int *status, void *stream)
 {
+    if (ctx && (param_mask < 1 || param_mask > 127))
+        return set_err(ctx, OED_EINVAL, "oed_hessian_map: param_mask must be in 1..127");
     if (!ctx) return OED_EINVAL;
     if (iters < 0 || iters > 100) return set_err(ctx, OED_EINVAL, "oed_hessian_map: iters must be in 0..100");
     if (n < 0 || (n > 0 && (!theta || !y || !H || !grad))) return set_err(ctx, OED_EINVAL, "oed_hessian_map: bad pointers");
@@ -554,7 +557,7 @@ int oed_hessian_map(oed_ctx *ctx, double *theta, int n, const double *y, const d
         rc = oed_hessian_ii(ctx, theta, n, y, sigma, H, grad, status, stream);
         if (rc) return rc;
         if (it == iters) break;
-        rc = oed_newton_step(H, grad, n, lo, hi, theta, nullptr, stream);
+        rc = oed_newton_step(H, grad, n, lo, hi, param_mask, theta, nullptr, stream);
         if (rc) return set_err(ctx, rc, "oed_hessian_map: Newton step");
     }
     return OED_OK;

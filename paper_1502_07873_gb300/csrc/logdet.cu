@@ -186,60 +186,67 @@ __global__ void __launch_bounds__(256) k_designs(const double *__restrict__ H_re
     }
 }
 
-// One Newton step per node on the cost L (Thm 1's estimator): solve H d = -grad with
-// the scaled Cholesky of H (S^-1 H S^-1 = L L^T), theta += d, clamped to the prior
-// box.  A node whose H is not positive definite keeps its theta (status OED_ENOTPD).
-__global__ void k_newton(const double *__restrict__ H, const double *__restrict__ grad, int n,
+// One Newton step per node on the cost L (Thm 1's estimator) over the unknown
+// parameters F (bit j of pmask): solve H_FF d = -grad_F with the scaled Cholesky of
+// H_FF (S^-1 H_FF S^-1 = L L^T), theta_F += d, clamped to the prior box; the known
+// parameters are left alone.  A node whose H_FF is not positive definite keeps its
+// theta (status OED_ENOTPD).
+__global__ void k_newton(const double *__restrict__ H, const double *__restrict__ grad, int n, int pmask,
                          const double *__restrict__ lohi, double *__restrict__ theta, int *__restrict__ status)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    int idx[kNT], k = 0;
+    for (int j = 0; j < kNT; j++)
+        if (pmask >> j & 1) idx[k++] = j;
     const double *h = H + (size_t)i * 49;
+    auto Hf = [&](int a, int b) { return h[idx[a] * kNT + idx[b]]; };
     double S[kNT], L[kNT][kNT], y[kNT];
     int bad = 0;
-    for (int a = 0; a < kNT; a++) {
-        const double d = h[a * kNT + a];
+    for (int a = 0; a < k; a++) {
+        const double d = Hf(a, a);
         bad |= !(d > 0.0) || !isfinite(d);
         S[a] = bad ? 1.0 : sqrt(d);
     }
-    for (int j = 0; j < kNT && !bad; j++) {
-        double s = h[j * kNT + j] / (S[j] * S[j]);
-        for (int k = 0; k < j; k++) s -= L[j][k] * L[j][k];
+    for (int j = 0; j < k && !bad; j++) {
+        double s = Hf(j, j) / (S[j] * S[j]);
+        for (int c = 0; c < j; c++) s -= L[j][c] * L[j][c];
         if (!(s > 0.0) || !isfinite(s)) {
             bad = 1;
             break;
         }
         L[j][j] = sqrt(s);
-        for (int r = j + 1; r < kNT; r++) {
-            double t = h[r * kNT + j] / (S[r] * S[j]);
-            for (int k = 0; k < j; k++) t -= L[r][k] * L[j][k];
+        for (int r = j + 1; r < k; r++) {
+            double t = Hf(r, j) / (S[r] * S[j]);
+            for (int c = 0; c < j; c++) t -= L[r][c] * L[j][c];
             L[r][j] = t / L[j][j];
         }
     }
     if (!bad) {
-        // (S L L^T S) d = -grad:  L z = -S^-1 grad, L^T e = z, d = S^-1 e
-        for (int a = 0; a < kNT; a++) {
-            double t = -grad[(size_t)i * kNT + a] / S[a];
-            for (int k = 0; k < a; k++) t -= L[a][k] * y[k];
+        // (S L L^T S) d = -grad_F:  L z = -S^-1 grad_F, L^T e = z, d = S^-1 e
+        for (int a = 0; a < k; a++) {
+            double t = -grad[(size_t)i * kNT + idx[a]] / S[a];
+            for (int c = 0; c < a; c++) t -= L[a][c] * y[c];
             y[a] = t / L[a][a];
         }
-        for (int a = kNT - 1; a >= 0; a--) {
+        for (int a = k - 1; a >= 0; a--) {
             double t = y[a];
-            for (int k = a + 1; k < kNT; k++) t -= L[k][a] * y[k];
+            for (int c = a + 1; c < k; c++) t -= L[c][a] * y[c];
             y[a] = t / L[a][a];
         }
-        for (int a = 0; a < kNT; a++) {
-            const double v = theta[(size_t)i * kNT + a] + y[a] / S[a];
-            theta[(size_t)i * kNT + a] = fmin(fmax(v, lohi[a]), lohi[kNT + a]);
+        for (int a = 0; a < k; a++) {
+            const int j = idx[a];
+            const double v = theta[(size_t)i * kNT + j] + y[a] / S[a];
+            theta[(size_t)i * kNT + j] = fmin(fmax(v, lohi[j]), lohi[kNT + j]);
         }
     }
     if (status) status[i] = bad ? OED_ENOTPD : 0;
 }
 
-void launch_newton(const double *H, const double *grad, int n, const double *lohi, double *theta, int *status,
-                   cudaStream_t s)
+void launch_newton(const double *H, const double *grad, int n, int pmask, const double *lohi, double *theta,
+                   int *status, cudaStream_t s)
 {
-    if (n > 0) k_newton<<<(n + 127) / 128, 128, 0, s>>>(H, grad, n, lohi, theta, status);
+    if (n > 0) k_newton<<<(n + 127) / 128, 128, 0, s>>>(H, grad, n, pmask, lohi, theta, status);
 }
 
 struct LoHi {

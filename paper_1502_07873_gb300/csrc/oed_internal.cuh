@@ -184,8 +184,8 @@ void launch_eig(const double *H, int n, const double *w, double logvol, int pmas
 void launch_eig_designs(const double *H_rec, int n, int nrec, int nwin, int win,
                         const unsigned char *mask, int ndesign, const double *w, double logvol,
                         double *eig, int *n_bad, cudaStream_t s);
-void launch_newton(const double *H, const double *grad, int n, const double *lohi, double *theta, int *status,
-                   cudaStream_t s);
+void launch_newton(const double *H, const double *grad, int n, int pmask, const double *lohi, double *theta,
+                   int *status, cudaStream_t s);
 void launch_nodes_mc(const double *u, int M, const double *lo, const double *hi, double *theta,
                      double *w, cudaStream_t s);
 
