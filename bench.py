@@ -692,6 +692,45 @@ def run_paper_study(args, rank, world, local):
         P.oed_dlmc(g_o, eps, g_o, sigma, le, e_re, stream=stream)
         torch.cuda.synchronize()
         dl.append([N, float(e_ind.item()), float(e_re.item()), time.perf_counter() - t1])
+    # (c) Thm 3 (H_1 + H_II at the Newton estimate on noisy data) against Thm 4 on M = 1000
+    #     Monte Carlo nodes, FP64 stencil, one noise realisation per node
+    M3 = 1000
+    ctx3 = P.Context(P.problem_from_workload(w, P.OED_FP64), max_solves=7 * 1024)
+    ctx3.jacobian = P.OED_JAC_SENSITIVITY
+    th3 = torch.tensor(W.paper_study_thetas(np.random.default_rng(45).random((M3, 3))), device=dev)
+    g3 = torch.empty((M3, w.nlevels, w.nrec, 2), dtype=torch.float64, device=dev)
+    P.oed_forward(ctx3, th3, g3, stream=stream)
+    y3 = g3 + sigma * torch.randn(g3.shape, dtype=torch.float64, device=dev, generator=gen)
+    w3 = torch.full((M3,), 1.0 / M3, dtype=torch.float64, device=dev)
+    H3 = torch.empty((M3, 7, 7), dtype=torch.float64, device=dev)
+    gr3 = torch.empty((M3, 7), dtype=torch.float64, device=dev)
+    e4 = torch.empty(1, dtype=torch.float64, device=dev)
+    e3 = torch.empty(1, dtype=torch.float64, device=dev)
+    nb3 = torch.empty(1, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    P.oed_hessian(ctx3, th3, w.prior_lo, w.prior_hi, w.rel_step, sigma, H3, stream=stream)
+    P.oed_eig_subset(ctx3, H3, w3, w.prior_lo, w.prior_hi, unknown, e4, stream=stream)
+    torch.cuda.synchronize()
+    t_thm4 = time.perf_counter() - t1
+    H3.zero_()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    P.oed_hessian_ii(ctx3, th3, y3, sigma, H3, grad=gr3, stream=stream)   # one primal + one dual per node
+    torch.cuda.synchronize()
+    t_hii = time.perf_counter() - t1
+    theta_hat = th3.clone()
+    t1 = time.perf_counter()
+    P.oed_hessian_map(ctx3, theta_hat, y3, w.prior_lo, w.prior_hi, w.rel_step, sigma, 4, H3, gr3, free=unknown,
+                      stream=stream)
+    P.oed_eig_subset(ctx3, H3, w3, w.prior_lo, w.prior_hi, unknown, e3, n_bad=nb3, stream=stream)
+    torch.cuda.synchronize()
+    t_thm3 = time.perf_counter() - t1
+    thm3 = {"nodes": M3, "thm4_eig": float(e4.item()), "thm3_eig": float(e3.item()),
+            "thm3_not_pd": int(nb3.item()), "newton_iterations": 4, "seconds_thm4": t_thm4,
+            "seconds_thm3": t_thm3, "seconds_h_ii": t_hii,
+            "h_ii_gcell_upd_per_s": 2 * w.cells * w.nsteps * M3 / t_hii / 1e9,
+            "note": "H_II: one primal and one dual solve per node (FP64), Gcell-updates of both"}
     out = {"metric": "Sec. 4.3-4.4: Laplace EIG convergence and Laplace vs double-loop MC",
            "workload": w.name, "unknown": ["theta_2 (depth)", "theta_4 (omega)", "theta_5 (m_xx)"],
            "sigma": sigma, "stencil_kernel": kernel_label(tuning),
@@ -702,7 +741,8 @@ def run_paper_study(args, rank, world, local):
            "seconds_sparse": t_sparse, "seconds_mc": t_mc,
            "dlmc_columns": ["N = M", "independent inner samples", "inner = outer samples (reused)",
                             "seconds"],
-           "dlmc": dl, "dlmc_reused_rel_to_laplace": [(d[2] - ref) / abs(ref) for d in dl]}
+           "dlmc": dl, "dlmc_reused_rel_to_laplace": [(d[2] - ref) / abs(ref) for d in dl],
+           "thm3_vs_thm4": thm3}
     if rank == 0:
         print(json.dumps(out))
 

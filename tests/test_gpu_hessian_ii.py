@@ -210,3 +210,24 @@ def test_thm3_gain_against_the_definition(P, oracle):
         assert r["not_pd"] <= N // 100   # an estimate at the box edge can leave H_1 + H_II indefinite
         for gap, se in ((r["gap4"], r["se4"]), (r["gap3"], r["se3"])):
             assert abs(gap) < max(4 * se, 0.005 * r["brute"]) and abs(gap) < 0.015 * r["brute"], (sg, r)
+
+
+def test_hessian_ii_paper_model_one_node(P, oracle):
+    """H_II and the gradient at the scale of the paper's model problem (101x76, two layers,
+    T = 1.25 s, two receivers, sigma = 0.01) against the oracle at one node, FP64."""
+    w = W.paper_study_model()
+    G = oracle.Grid.from_workload(w)
+    th = W.paper_study_thetas(np.random.default_rng(45).random((1, 3)))
+    sigma = 0.01
+    y = oracle.forward(G, th[0]) + sigma * np.random.default_rng(0).standard_normal((w.nlevels, w.nrec, 2))
+    H2, g2 = oracle.hessian_ii(G, th[0], y, sigma)
+    H1 = oracle.node_hessian_sensitivity(G, th[0], sigma)
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP64), max_solves=4)
+    H = torch.zeros((1, 7, 7), dtype=torch.float64, device=DEV)
+    gr = torch.empty((1, 7), dtype=torch.float64, device=DEV)
+    P.oed_hessian_ii(ctx, _t(th), _t(y[None]), sigma, H, grad=gr)
+    torch.cuda.synchronize()
+    d = np.sqrt(np.diag(H1))
+    assert np.max(np.abs(H[0].cpu().numpy() - H2) / np.outer(d, d)) <= 1e-9
+    rnorm = np.sqrt(np.sum((y - oracle.forward(G, th[0])) ** 2)) / sigma
+    assert np.max(np.abs(gr[0].cpu().numpy() - g2) / (d * rnorm)) <= 1e-9
