@@ -93,34 +93,6 @@ __device__ __forceinline__ float2 ld_cluster2(unsigned addr)
     return v;
 }
 
-// One grid row as seen by the thread owning columns (c, c+1): per component the
-// two centre values, the two (e - c) - (c - w) second differences, the two
-// east - west differences (cross terms of the other component) and, once the row
-// below is known, the two south differences (row below minus this row).
-struct Row2 {
-    float xa, xb, za, zb;
-    float lxa, lxb, lza, lzb;
-    float dxa, dxb, dza, dzb;
-    float vxa, vxb, vza, vzb;
-};
-
-// w = (x, z) of the west column, m = the pair, e = (x, z) of the east column
-__device__ __forceinline__ void row_from(float2 w, float4 m, float2 e, Row2 &r)
-{
-    r.xa = m.x;
-    r.za = m.y;
-    r.xb = m.z;
-    r.zb = m.w;
-    r.lxa = (m.z - m.x) - (m.x - w.x);
-    r.lxb = (e.x - m.z) - (m.z - m.x);
-    r.lza = (m.w - m.y) - (m.y - w.y);
-    r.lzb = (e.y - m.w) - (m.w - m.y);
-    r.dxa = m.z - w.x;
-    r.dxb = e.x - m.x;
-    r.dza = m.w - w.y;
-    r.dzb = e.y - m.y;
-}
-
 // q points at the thread's own slot of a local row
 __device__ __forceinline__ void load_row(const float4 *q, Row2 &r)
 {
@@ -134,57 +106,6 @@ __device__ __forceinline__ void load_row_remote(const float4 *q, unsigned nb, Ro
 {
     const unsigned b = remote_addr(smem_addr(q), nb);
     row_from(ld_cluster2(b - 8u), ld_cluster4(b), ld_cluster2(b + 16u), r);
-}
-
-// south differences of row c once its south row s is loaded
-__device__ __forceinline__ void south(Row2 &c, const Row2 &s)
-{
-    c.vxa = s.xa - c.xa;
-    c.vxb = s.xb - c.xb;
-    c.vza = s.za - c.za;
-    c.vzb = s.zb - c.zb;
-}
-
-// u^{m+1} of the pair from the rows n, c, s (the node update of stencil_cell.cuh);
-// n supplies the north differences (its south ones) and the north cross terms.
-// u holds u^{m-1} on entry, in slot order (x_a, z_a, x_b, z_b).
-__device__ __forceinline__ void pair_update(const FacCoef<float> &K, const Row2 &n, const Row2 &c,
-                                            const Row2 &s, float4 &u)
-{
-    u.x = leap(c.xa, u.x, op_x(K, c.lxa, c.vxa, n.vxa, s.dza, n.dza));
-    u.z = leap(c.xb, u.z, op_x(K, c.lxb, c.vxb, n.vxb, s.dzb, n.dzb));
-    u.y = leap(c.za, u.y, op_z(K, c.lza, c.vza, n.vza, s.dxa, n.dxa));
-    u.w = leap(c.zb, u.w, op_z(K, c.lzb, c.vzb, n.vzb, s.dxb, n.dxb));
-}
-
-// Absorbing rows: the bottom row from its north neighbour, then the side columns
-// (which take precedence at the corners) from their interior neighbour.  kind:
-// bit 0 node c is column 0, bit 1 node c+1 is column nx-1, bit 2 node c is column
-// nx-1 (node c+1 is then the ghost and stays zero).
-// (nv: the north row's slot, used by the bottom row only)
-__device__ __forceinline__ void absorbing(float cp, float cs, float4 nv, const Row2 &c, bool bottom,
-                                          int kind, float4 &u)
-{
-    if (bottom) {
-        u.x = absorb(c.xa, nv.x, cs);
-        u.z = absorb(c.xb, nv.z, cs);
-        u.y = absorb(c.za, nv.y, cp);
-        u.w = absorb(c.zb, nv.w, cp);
-    }
-    if (kind & 1) {
-        u.x = absorb(c.xa, c.xb, cp);
-        u.y = absorb(c.za, c.zb, cs);
-    }
-    if (kind & 2) {
-        u.z = absorb(c.xb, c.xa, cp);
-        u.w = absorb(c.zb, c.za, cs);
-    }
-    if (kind & 4) {   // column nx-1: its east - west difference is -west (the ghost east is 0)
-        u.x = absorb(c.xa, -c.dxa, cp);
-        u.y = absorb(c.za, -c.dza, cs);
-        u.z = 0.0f;
-        u.w = 0.0f;
-    }
 }
 
 // float offset of node (column i, component comp) within a shared row

@@ -1,21 +1,25 @@
 // Streaming leap-frog step with TMA tile loads (one launch per time step, for
 // grids whose wavefield does not fit the cluster-resident kernel; Sec. 3.3.1,
-// Eq. Full_Disc; node update from stencil_cell.cuh).
+// Eq. Full_Disc; the column-pair node update of stencil_cell.cuh).
 //
-// A persistent CTA walks tiles (solve, 16-row band, 64-column band) of the batch.
+// A persistent CTA walks tiles (solve, 20-row band, 64-column band) of the batch.
 // Its producer warp issues, for each tile, four cp.async.bulk.tensor loads into one
-// stage of a shared-memory ring: u_x and u_z of level m with a halo (rows z0-1 ..
-// z0+16, columns x0-4 .. x0+67; the x start stays a multiple of four floats so
+// stage of a shared-memory ring -- u_x and u_z of level m with a halo (rows z0-1 ..
+// z0+20, columns x0-4 .. x0+67; the x start stays a multiple of four floats so
 // every copy starts on a 16-byte boundary, the grid edges read as zeros and are
-// never used) and u_x, u_z of level m-1 without halo.  Completion is tracked by
-// an mbarrier per stage (expect_tx of the stage's bytes); the consumer warps wait
-// on it, compute the tile from shared memory with a register window per column,
-// store u^{m+1} with streaming stores over u^{m-1}, and release the stage on a
-// second mbarrier.  Every wait is bounded: on expiry the kernel raises a device
+// never used) and u_x, u_z of level m-1 without halo -- and one cp.async.bulk of the
+// band's per-row coefficients.  Completion is tracked by an mbarrier per stage
+// (expect_tx of the stage's bytes).  Two groups of four consumer warps take the
+// tiles in turn, each with two stages of its own, so each barrier is waited on
+// phase after phase by one group only (a group that waited on another group's
+// stage could see a phase two uses old and read a stage still being filled).  In
+// a tile a thread owns a column pair and marches five rows with the register
+// window of the resident kernel (each row's differences formed once), stores
+// u^{m+1} with streaming stores over u^{m-1}, and the group releases the stage on
+// a second mbarrier.  Every wait is bounded: on expiry the kernel raises a device
 // flag, the producer waits (bounded) for its copies in flight, and the threads
-// return; the flag turns the affected nodes' status into OED_ETIMEOUT.
-// HBM traffic per cell-update is the algorithmic 24 B (FP32); the halo re-reads
-// come from L2.
+// return; the flag turns the affected nodes' status into OED_ETIMEOUT.  HBM traffic
+// per cell-update is the algorithmic 24 B (FP32); the halo re-reads come from L2.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -23,16 +27,20 @@
 
 namespace oed {
 
-constexpr int kTX = 64, kTZ = 16, kHX = 4;
+constexpr int kTX = 64, kTZ = 20, kHX = 4;
 constexpr int kWX = kTX + 2 * kHX, kWZ = kTZ + 2;
-constexpr int kStages = 4;
-constexpr int kConsumerWarps = 8;                       // 64 columns x 4 segments of 4 rows
-constexpr int kRowsPerSeg = kTZ / (kConsumerWarps / 2); // 4
-constexpr int kHaloBytes = kWX * kWZ * 4;               // 5184
-constexpr int kHaloPad = (kHaloBytes + 127) / 128 * 128;  // 5248
-constexpr int kPlainBytes = kTX * kTZ * 4;              // 4096
-constexpr int kStageBytes = 2 * kHaloPad + 2 * kPlainBytes;
-constexpr unsigned kTxBytes = 2 * kHaloBytes + 2 * kPlainBytes;
+constexpr int kGroups = 2;                               // consumer groups, tiles taken in turn
+constexpr int kGroupStages = 2;                          // ring stages owned by each group
+constexpr int kStages = kGroups * kGroupStages;
+constexpr int kGroupWarps = 4;                           // 32 column pairs x 4 segments
+constexpr int kConsumerWarps = kGroups * kGroupWarps;
+constexpr int kRowsPerSeg = kTZ / kGroupWarps;           // 5
+constexpr int kHaloBytes = kWX * kWZ * 4;                // 6336
+constexpr int kHaloPad = (kHaloBytes + 127) / 128 * 128; // 6400
+constexpr int kPlainBytes = kTX * kTZ * 4;               // 5120
+constexpr int kCoefBytes = kTZ * (int)sizeof(FacCoef<float>);   // 1280
+constexpr int kStageBytes = 2 * kHaloPad + 2 * kPlainBytes + kCoefBytes;
+constexpr unsigned kTileTxBytes = 2 * kHaloBytes + 2 * kPlainBytes;
 constexpr unsigned long long kWaitLimitNs = 2000000000ULL;   // 2 s per wait
 constexpr int kSmemBytes = kStages * kStageBytes + 128 /* alignment slack */ + 128 /* barriers */;
 
@@ -103,6 +111,35 @@ __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, int
         : "memory");
 }
 
+// 1-D bulk copy global -> shared, completion on an mbarrier (16-byte aligned, size a
+// multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(bar))
+                 : "memory");
+}
+
+// stage and phase of the CTA's k-th tile: group k % kGroups takes it as its i-th
+// tile, i = k / kGroups, in one of the group's own stages
+__device__ __forceinline__ int tile_stage(long long k)
+{
+    return (int)(k % kGroups) * kGroupStages + (int)((k / kGroups) % kGroupStages);
+}
+__device__ __forceinline__ unsigned tile_phase(long long k)
+{
+    return (unsigned)(((k / kGroups) / kGroupStages) & 1);
+}
+
+// the row of a tile seen by the thread owning pair p (columns x0 + 2p, x0 + 2p + 1)
+__device__ __forceinline__ void tile_row(const float *hx, const float *hz, int r, int p, Row2 &row)
+{
+    const float *qx = hx + r * kWX + kHX + 2 * p, *qz = hz + r * kWX + kHX + 2 * p;
+    const float2 mx = *reinterpret_cast<const float2 *>(qx), mz = *reinterpret_cast<const float2 *>(qz);
+    row_from(make_float2(qx[-1], qz[-1]), make_float4(mx.x, mz.x, mx.y, mz.y), make_float2(qx[2], qz[2]), row);
+}
+
 __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
     k_step_tma(TmaArgs a, const __grid_constant__ CUtensorMap cur_halo,
                const __grid_constant__ CUtensorMap nxt_plain)
@@ -120,7 +157,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], kConsumerWarps);
+            mbar_init(&empty_bar[s], kGroupWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -132,9 +169,9 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
             long long k = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < ntile; t += gridDim.x, k++) {
-                const int stage = (int)(k % kStages);
-                const unsigned phase = (unsigned)((k / kStages) & 1);
-                if (k >= kStages && !mbar_wait(&empty_bar[stage], phase ^ 1u)) {
+                const int stage = tile_stage(k);
+                const unsigned phase = tile_phase(k);
+                if (k / kGroups >= kGroupStages && !mbar_wait(&empty_bar[stage], phase ^ 1u)) {
                     ok = false;
                     break;
                 }
@@ -143,31 +180,34 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
                 const int s = (int)(t / ((long long)a.nbx * a.nbz));
                 const int x0 = bx * kTX, z0 = bz * kTZ;
                 unsigned char *st = smem + stage * kStageBytes;
-                mbar_expect_tx(&full_bar[stage], kTxBytes);
+                const int nrow = min(kTZ, g.nz - z0);   // coefficient rows of the band
+                mbar_expect_tx(&full_bar[stage], kTileTxBytes + (unsigned)(nrow * (int)sizeof(FacCoef<float>)));
                 tma_load3(st, &cur_halo, x0 - kHX, z0 - 1, 2 * s, &full_bar[stage]);
                 tma_load3(st + kHaloPad, &cur_halo, x0 - kHX, z0 - 1, 2 * s + 1, &full_bar[stage]);
                 tma_load3(st + 2 * kHaloPad, &nxt_plain, x0, z0, 2 * s, &full_bar[stage]);
                 tma_load3(st + 2 * kHaloPad + kPlainBytes, &nxt_plain, x0, z0, 2 * s + 1, &full_bar[stage]);
+                bulk_load(st + 2 * kHaloPad + 2 * kPlainBytes, a.fac + z0, (unsigned)(nrow * (int)sizeof(FacCoef<float>)),
+                          &full_bar[stage]);
             }
             if (!ok) {
                 atomicExch(a.err, 1);
                 // copies already issued for the last stages must land before the CTA exits
                 for (long long j = (k > kStages ? k - kStages : 0); j < k; j++)
-                    mbar_wait(&full_bar[j % kStages], (unsigned)((j / kStages) & 1));
+                    mbar_wait(&full_bar[tile_stage(j)], tile_phase(j));
             }
         }
         return;
     }
 
-    // consumers: thread -> column cx of the tile and a segment of kRowsPerSeg rows
-    const int ct = threadIdx.x - 32;
-    const int cx = ct % kTX;
-    const int seg = ct / kTX;
-    long long k = 0;
-    for (long long t = blockIdx.x; t < ntile; t += gridDim.x, k++) {
-        const int stage = (int)(k % kStages);
-        const unsigned phase = (unsigned)((k / kStages) & 1);
-        if (!mbar_wait(&full_bar[stage], phase)) {
+    // consumers: group grp takes the CTA's tiles k = grp, grp + kGroups, ...; within a
+    // tile, lane p owns the column pair p and warp wig the rows [5 wig, 5 wig + 5)
+    const int grp = (warp - 1) / kGroupWarps, wig = (warp - 1) % kGroupWarps;
+    const int gt = wig * 32 + lane;   // thread index within the group
+    const int p = lane;
+    for (long long k = grp, t = blockIdx.x + (long long)grp * gridDim.x; t < ntile;
+         k += kGroups, t += (long long)kGroups * gridDim.x) {
+        const int stage = tile_stage(k);
+        if (!mbar_wait(&full_bar[stage], tile_phase(k))) {
             atomicExch(a.err, 1);
             return;
         }
@@ -179,61 +219,66 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
         const float *hz = hx + kHaloPad / 4;
         const float *px = hx + 2 * kHaloPad / 4;
         const float *pz = px + kPlainBytes / 4;
-        // receiver samples of level m on the surface band
+        const FacCoef<float> *cf = reinterpret_cast<const FacCoef<float> *>(px + 2 * kPlainBytes / 4);
+        // receiver samples of level m on the surface band (halo row 1 is grid row 0)
         if (z0 == 0)
-            for (int q = ct; q < 2 * g.nrec; q += 32 * kConsumerWarps) {
+            for (int q = gt; q < 2 * g.nrec; q += 32 * kGroupWarps) {
                 const int xr = a.rec[q >> 1] - x0;
                 if (xr >= 0 && xr < kTX)
                     a.trace[((size_t)s * g.nlev + a.m) * g.nrec * 2 + q] = ((q & 1) ? hz : hx)[kWX + xr + kHX];
             }
-        const int x = x0 + cx;
+        const int x = x0 + 2 * p;
         if (x < g.nx) {
-            const int side = (x == 0) ? 1 : ((x == g.nx - 1) ? 2 : 0);
+            const int kind = (x == 0 ? 1 : 0) | (x + 1 == g.nx - 1 ? 2 : 0) | (x == g.nx - 1 ? 4 : 0);
             const SourceDesc<float> *sd = a.src + s;
-            const int si = x - sd->i0;
-            const bool scol = (unsigned)si < (unsigned)kPatch;
-            const float S = scol ? a.stf[(size_t)s * g.nsteps + a.m] : 0.0f;
+            const int siA = x - sd->i0, siB = x + 1 - sd->i0;
+            const bool scolA = (unsigned)siA < (unsigned)kPatch;
+            const bool scolB = x + 1 < g.nx && (unsigned)siB < (unsigned)kPatch;
+            const float S = (scolA || scolB) ? a.stf[(size_t)s * g.nsteps + a.m] : 0.0f;
             float *gx = a.nxt + (size_t)s * g.solve_stride;
             float *gz = gx + g.comp_stride;
-            const int r0 = seg * kRowsPerSeg;
-            float W[3][3], Z[3][3];
-            // halo rows r0 and r0 + 1 (grid rows z0 + r0 - 1, z0 + r0)
-#pragma unroll
-            for (int q = 0; q < 2; q++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    W[q][c] = hx[(r0 + q) * kWX + cx + kHX - 1 + c];
-                    Z[q][c] = hz[(r0 + q) * kWX + cx + kHX - 1 + c];
-                }
+            const int r0 = wig * kRowsPerSeg;
+            Row2 rn, rc, rs;
+            tile_row(hx, hz, r0, p, rn);       // grid row z0 + r0 - 1
+            tile_row(hx, hz, r0 + 1, p, rc);   // grid row z0 + r0
+            south(rn, rc);
 #pragma unroll
             for (int r = r0; r < r0 + kRowsPerSeg; r++) {
                 const int z = z0 + r;
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    W[2][c] = hx[(r + 2) * kWX + cx + kHX - 1 + c];
-                    Z[2][c] = hz[(r + 2) * kWX + cx + kHX - 1 + c];
+                if (z >= g.nz) break;
+                tile_row(hx, hz, r + 2, p, rs);
+                south(rc, rs);
+                const float2 ux = *reinterpret_cast<const float2 *>(px + r * kTX + 2 * p);
+                const float2 uz = *reinterpret_cast<const float2 *>(pz + r * kTX + 2 * p);
+                float4 u = make_float4(ux.x, uz.x, ux.y, uz.y);
+                const FacCoef<float> K = cf[r];
+                if (z == g.nz - 1) {
+                    absorbing(K.cp, K.cs, make_float4(rn.xa, rn.za, rn.xb, rn.zb), rc, true, kind, u);
+                } else if (z == 0) {   // surface row: no north differences, cross terms on the row itself
+                    Row2 nt = rc;
+                    nt.vxa = nt.vxb = nt.vza = nt.vzb = 0.0f;
+                    pair_update(K, nt, rc, rs, u);
+                    if (kind) absorbing(K.cp, K.cs, u, rc, false, kind, u);
+                } else {
+                    pair_update(K, rn, rc, rs, u);
+                    if (kind) absorbing(K.cp, K.cs, u, rc, false, kind, u);
                 }
-                if (z < g.nz) {
-                    const FacCoef<float> K = a.fac[z];
-                    float ux, uz;
-                    node_update(K, W[0], W[1], W[2], Z[0], Z[1], Z[2], px[r * kTX + cx], pz[r * kTX + cx],
-                                side, z == g.nz - 1, z == 0, ux, uz);
-                    const int b = z - sd->j0;
-                    if (scol && (unsigned)b < (unsigned)kPatch && !side && z != g.nz - 1) {
-                        ux = add_force(ux, S, sd->wx[b * kPatch + si]);
-                        uz = add_force(uz, S, sd->wz[b * kPatch + si]);
+                const int b = z - sd->j0;
+                if ((unsigned)b < (unsigned)kPatch) {   // force term on the patch nodes (zero off it)
+                    if (scolA) {
+                        u.x = add_force(u.x, S, sd->wx[b * kPatch + siA]);
+                        u.y = add_force(u.y, S, sd->wz[b * kPatch + siA]);
                     }
-                    const size_t o = (size_t)z * g.xp + x;
-                    __stcs(gx + o, ux);
-                    __stcs(gz + o, uz);
+                    if (scolB) {
+                        u.z = add_force(u.z, S, sd->wx[b * kPatch + siB]);
+                        u.w = add_force(u.w, S, sd->wz[b * kPatch + siB]);
+                    }
                 }
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    W[0][c] = W[1][c];
-                    W[1][c] = W[2][c];
-                    Z[0][c] = Z[1][c];
-                    Z[1][c] = Z[2][c];
-                }
+                const size_t o = (size_t)z * g.xp + x;
+                __stcs(reinterpret_cast<float2 *>(gx + o), make_float2(u.x, u.z));
+                __stcs(reinterpret_cast<float2 *>(gz + o), make_float2(u.y, u.w));
+                rn = rc;
+                rc = rs;
             }
         }
         __syncwarp();

@@ -460,3 +460,25 @@ def test_full_size_batched_sampled(P, oracle):
     P.oed_forward(ctx, _t(th[[5, 200]]), g)
     for k, i in enumerate((5, 200)):
         assert _normwise(g[k].cpu().numpy(), oracle.forward(G, th[i])) <= 1e-4
+
+
+def test_tma_kernel_many_tiles_per_cta_bitwise(P):
+    """The TMA streaming kernel with several tiles per persistent CTA, so every stage of the
+    ring is refilled and both consumer groups cycle through their stages: 401x201, 20 solves
+    (1540 tiles over at most 304 CTAs), 400 steps (the waves reach the receivers), bit for
+    bit against the register streaming kernel, twice (the second run replays the graph)."""
+    w = W.tiny(nx=401, nz=201, h=5.0, nsteps=400, nrec=20)
+    rng = np.random.default_rng(77)
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+    th = lo + (hi - lo) * rng.random((20, 7))
+    th[:, 2] = lo[2]   # earliest start
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=20)
+    g_ref = torch.empty((20, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
+    P.oed_forward(ctx, _t(th), g_ref)
+    ctx.set_tuning(-1, 4, 4)
+    g = torch.empty_like(g_ref)
+    for _ in range(2):
+        P.oed_forward(ctx, _t(th), g)
+        torch.cuda.synchronize()
+        assert torch.equal(g, g_ref)
+    assert float(g_ref.abs().max()) > 1e-3
