@@ -123,13 +123,23 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 
 // stage and phase of the CTA's k-th tile: group k % kGroups takes it as its i-th
 // tile, i = k / kGroups, in one of the group's own stages
-__device__ __forceinline__ int tile_stage(long long k)
+__device__ __forceinline__ int tile_stage(unsigned k)
 {
     return (int)(k % kGroups) * kGroupStages + (int)((k / kGroups) % kGroupStages);
 }
-__device__ __forceinline__ unsigned tile_phase(long long k)
+__device__ __forceinline__ unsigned tile_phase(unsigned k)
 {
-    return (unsigned)(((k / kGroups) / kGroupStages) & 1);
+    return ((k / kGroups) / kGroupStages) & 1u;
+}
+
+// (column band, row band, solve) of tile t; 32-bit arithmetic (the host keeps the tile
+// count below 2^31)
+__device__ __forceinline__ void tile_coords(unsigned t, const TmaArgs &a, int &bx, int &bz, int &s)
+{
+    const unsigned q = t / (unsigned)a.nbx;
+    bx = (int)(t - q * (unsigned)a.nbx);
+    s = (int)(q / (unsigned)a.nbz);
+    bz = (int)(q - (unsigned)s * (unsigned)a.nbz);
 }
 
 // the row of a tile seen by the thread owning pair p (columns x0 + 2p, x0 + 2p + 1)
@@ -153,7 +163,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
     uint64_t *empty_bar = full_bar + kStages;
     const Geometry &g = a.g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long ntile = (long long)a.nsolve * a.nbz * a.nbx;
+    const unsigned ntile = (unsigned)a.nsolve * (unsigned)a.nbz * (unsigned)a.nbx;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
             mbar_init(&full_bar[s], 1);
@@ -166,18 +176,17 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
     if (warp == 0) {
         // producer
         if (lane == 0) {
-            long long k = 0;
+            unsigned k = 0;
             bool ok = true;
-            for (long long t = blockIdx.x; t < ntile; t += gridDim.x, k++) {
+            for (unsigned t = blockIdx.x; t < ntile; t += gridDim.x, k++) {
                 const int stage = tile_stage(k);
                 const unsigned phase = tile_phase(k);
                 if (k / kGroups >= kGroupStages && !mbar_wait(&empty_bar[stage], phase ^ 1u)) {
                     ok = false;
                     break;
                 }
-                const int bx = (int)(t % a.nbx);
-                const int bz = (int)((t / a.nbx) % a.nbz);
-                const int s = (int)(t / ((long long)a.nbx * a.nbz));
+                int bx, bz, s;
+                tile_coords(t, a, bx, bz, s);
                 const int x0 = bx * kTX, z0 = bz * kTZ;
                 unsigned char *st = smem + stage * kStageBytes;
                 const int nrow = min(kTZ, g.nz - z0);   // coefficient rows of the band
@@ -192,7 +201,7 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
             if (!ok) {
                 atomicExch(a.err, 1);
                 // copies already issued for the last stages must land before the CTA exits
-                for (long long j = (k > kStages ? k - kStages : 0); j < k; j++)
+                for (unsigned j = (k > kStages ? k - kStages : 0); j < k; j++)
                     mbar_wait(&full_bar[tile_stage(j)], tile_phase(j));
             }
         }
@@ -204,16 +213,14 @@ __global__ void __launch_bounds__(32 * (kConsumerWarps + 1), 2)
     const int grp = (warp - 1) / kGroupWarps, wig = (warp - 1) % kGroupWarps;
     const int gt = wig * 32 + lane;   // thread index within the group
     const int p = lane;
-    for (long long k = grp, t = blockIdx.x + (long long)grp * gridDim.x; t < ntile;
-         k += kGroups, t += (long long)kGroups * gridDim.x) {
+    for (unsigned k = grp, t = blockIdx.x + grp * gridDim.x; t < ntile; k += kGroups, t += kGroups * gridDim.x) {
         const int stage = tile_stage(k);
         if (!mbar_wait(&full_bar[stage], tile_phase(k))) {
             atomicExch(a.err, 1);
             return;
         }
-        const int bx = (int)(t % a.nbx);
-        const int bz = (int)((t / a.nbx) % a.nbz);
-        const int s = (int)(t / ((long long)a.nbx * a.nbz));
+        int bx, bz, s;
+        tile_coords(t, a, bx, bz, s);
         const int x0 = bx * kTX, z0 = bz * kTZ;
         const float *hx = reinterpret_cast<const float *>(smem + stage * kStageBytes);
         const float *hz = hx + kHaloPad / 4;
@@ -359,6 +366,7 @@ cudaError_t launch_steps_tma(const oed_ctx *ctx, int nsolve, cudaStream_t st, cu
     a.nbx = (g.nx + kTX - 1) / kTX;
     a.nbz = (g.nz + kTZ - 1) / kTZ;
     const long long ntile = (long long)nsolve * a.nbx * a.nbz;
+    if (ntile >= (1LL << 31) - 2LL * ctx->tma_ctas) return cudaErrorInvalidValue;   // 32-bit tile indices
     const int grid = (int)(ntile < (long long)ctx->tma_ctas ? ntile : (long long)ctx->tma_ctas);
     const int nsteps = (nsteps_override > 0 && nsteps_override < g.nsteps) ? nsteps_override : g.nsteps;
     float *u0 = (float *)ctx->d_u0, *u1 = (float *)ctx->d_u1;
