@@ -4,7 +4,9 @@
 //
 // CTA r of a cluster of C owns rows [r R, min((r+1) R, nz)) of the grid, both
 // components and both time levels, in its shared memory:
-//     A, B : [R][npair + 2] float4,   coef : [R] FacCoef
+//     A, B : [R][npair + 2] float4,   coef : [R] FacCoef,   the solve's 2 x 49
+//     source weights (kept on chip: read from global memory every step they put an L1
+//     round trip on the critical path of the warps that own the patch columns)
 // Slot q of a row holds the column pair p = q - 1 as (x_2p, z_2p, x_2p+1, z_2p+1);
 // slots 0 and npair + 1 (columns -2, -1, nx.., and column nx when nx is odd) are
 // zero ghosts, so a thread owning pair p reads its whole neighbourhood with one
@@ -131,6 +133,9 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
 
     for (int k = tid; k < 2 * lvl; k += nthr) smem4[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int k = tid; k < nrows; k += nthr) coef[k] = a.fac[j0 + k];
+    float *sw = reinterpret_cast<float *>(coef + R);   // this solve's source weights, x then z
+    for (int k = tid; k < 2 * kPatch * kPatch; k += nthr)
+        sw[k] = k < kPatch * kPatch ? a.src[blockIdx.y].wx[k] : a.src[blockIdx.y].wz[k - kPatch * kPatch];
 
     // threads are packed densely over (segment, pair): a warp may straddle two segments
     const int p = tid % a.npair;
@@ -257,14 +262,14 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                     if (lj < l0 || lj >= l1) continue;
                     float *row = nf + (size_t)lj * sq * 4;
                     if (scolA) {
-                        row[node_off(c, 0)] = add_force(row[node_off(c, 0)], S, sd->wx[bb * kPatch + siA]);
-                        row[node_off(c, 1)] = add_force(row[node_off(c, 1)], S, sd->wz[bb * kPatch + siA]);
+                        row[node_off(c, 0)] = add_force(row[node_off(c, 0)], S, sw[bb * kPatch + siA]);
+                        row[node_off(c, 1)] = add_force(row[node_off(c, 1)], S, sw[kPatch * kPatch + bb * kPatch + siA]);
                     }
                     if (scolB) {
                         row[node_off(c + 1, 0)] =
-                            add_force(row[node_off(c + 1, 0)], S, sd->wx[bb * kPatch + siB]);
+                            add_force(row[node_off(c + 1, 0)], S, sw[bb * kPatch + siB]);
                         row[node_off(c + 1, 1)] =
-                            add_force(row[node_off(c + 1, 1)], S, sd->wz[bb * kPatch + siB]);
+                            add_force(row[node_off(c + 1, 1)], S, sw[kPatch * kPatch + bb * kPatch + siB]);
                     }
                 }
             }
@@ -293,7 +298,8 @@ static ResShape resident_shape(const Geometry &g, int C)
     const int R = (g.nz + C - 1) / C;
     if ((C - 1) * R >= g.nz) return r;   // a CTA would own no rows
     const int sq = npair + 2;   // ghost slots on both sides
-    const size_t smem = (size_t)2 * R * sq * sizeof(float4) + (size_t)R * sizeof(FacCoef<float>);
+    const size_t smem = (size_t)2 * R * sq * sizeof(float4) + (size_t)R * sizeof(FacCoef<float>) +
+                        2 * kPatch * kPatch * sizeof(float);
     if (smem > 227 * 1024) return r;
     int nseg = kResThreads / npair;
     if (nseg > R) nseg = R;

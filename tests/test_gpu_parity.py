@@ -482,3 +482,23 @@ def test_tma_kernel_many_tiles_per_cta_bitwise(P):
         torch.cuda.synchronize()
         assert torch.equal(g, g_ref)
     assert float(g_ref.abs().max()) > 1e-3
+
+
+def test_resident_one_row_per_cta(P, oracle):
+    """Eight CTAs of one row each (nz = 8, clusters of 8): the surface row's south row, every
+    north and south row and the absorbing bottom row's north row come from neighbouring CTAs'
+    shared memory.  Against the oracle (FP32 bar) and bit for bit against the streaming kernel."""
+    w = W.tiny(nx=40, nz=8, h=50.0, nsteps=80, nrec=3)
+    th = np.array([[1000.0, 120.0, 0.1, 6.0, 5e13, 2e13, 8e13], [930.0, 140.0, 0.15, 7.0, 9e13, 4e13, 1e13]])
+    G = oracle.Grid.from_workload(w)
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=4)
+    g_ref = torch.empty((2, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
+    P.oed_forward(ctx, _t(th), g_ref)
+    ctx.set_tuning(8, 4, 4)
+    g = torch.empty_like(g_ref)
+    P.oed_forward(ctx, _t(th), g)
+    torch.cuda.synchronize()
+    assert torch.equal(g, g_ref)
+    for k in range(2):
+        ref = oracle.forward(G, th[k])
+        assert _normwise(g[k].cpu().numpy(), ref) <= 1e-4
