@@ -12,6 +12,7 @@
  * plainly, with no blocking, fusion or reordering:
  *   ref_delta_1d       regularised delta / delta' weights   (Sec. 3.3.2, item 2)
  *   ref_stf            Gaussian source time function          (Sec. 4.1)
+ *   ref_ricker         Ricker wavelet, the optional alternative
  *   ref_media          Lame parameters from velocities        (Sec. 2.1, c_p, c_s)
  *   ref_source_patch   f = S(t) M grad(delta)                 (Eq. source, item 2)
  *   ref_step           one leap-frog step of the FD scheme    (Eqs. interior_disc,
@@ -145,6 +146,21 @@ double ref_stf(double t, double ts, double ws)
 {
     double s = t - ts;
     return ws / sqrt(2.0 * REF_PI) * exp(-ws * ws * s * s / 2.0);
+}
+
+/* Ricker wavelet with peak frequency f (Hz) centred at t_s, the conventional
+ * alternative source time function: r = (1 - 2a) exp(-a), a = (pi f (t - t_s))^2. */
+double ref_ricker(double t, double ts, double f)
+{
+    double a = REF_PI * f * (t - ts);
+    a = a * a;
+    return (1.0 - 2.0 * a) * exp(-a);
+}
+
+/* the time function of kind 0 (the paper's Gaussian) or 1 (Ricker) */
+static double stf_kind(int kind, double t, double ts, double w)
+{
+    return kind == 1 ? ref_ricker(t, ts, w) : ref_stf(t, ts, w);
 }
 
 /* Node media from a depth-layered model: layer l covers z_top[l] <= z < z_top[l+1];
@@ -303,9 +319,21 @@ void ref_step(const ref_grid *g, const double *ux, const double *uz, const doubl
  * samples g[m][r][c] = u_c(x_r, t_m) for m = 0..nsteps (Eq. forward_model).
  * Returns 0, or -1 if the source patch leaves the interior.
  * ------------------------------------------------------------------------- */
+int ref_forward_stf(int kind, int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                    const double *mu, const double *nu, int nrec, const int *rec_ix,
+                    const double *theta, double *g);
+
 int ref_forward(int nx, int nz, double h, double dt, int nsteps, const double *lam,
                 const double *mu, const double *nu, int nrec, const int *rec_ix,
                 const double *theta, double *g)
+{
+    return ref_forward_stf(0, nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, theta, g);
+}
+
+/* The same with the time function of the given kind (0 Gaussian, 1 Ricker). */
+int ref_forward_stf(int kind, int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                    const double *mu, const double *nu, int nrec, const int *rec_ix,
+                    const double *theta, double *g)
 {
     ref_grid G = {nx, nz, h, dt, lam, mu, nu};
     int i0, j0;
@@ -322,7 +350,7 @@ int ref_forward(int nx, int nz, double h, double dt, int nsteps, const double *l
         g[(0 * nrec + r) * 2 + 1] = 0.0;
     }
     for (int m = 0; m < nsteps; m++) {
-        double s = ref_stf(m * dt, theta[2], theta[3]);
+        double s = stf_kind(kind, m * dt, theta[2], theta[3]);
         for (int b = 0; b < 6; b++)
             for (int a = 0; a < 6; a++) {
                 size_t c = (size_t)(j0 + b) * nx + (i0 + a);
@@ -481,10 +509,25 @@ static int sens_solves(int nx, int nz, double h, double dt, int nsteps, const do
  *   H = sigma^-2 sum_{m <= nsteps} sum_r sum_c J^T J.
  * H_rec ([nrec][nwin][49]) may be NULL.  Returns 0 or -1 (source out of range).
  * ------------------------------------------------------------------------- */
+int ref_node_hessian_stf(int kind, int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                         const double *mu, const double *nu, int nrec, const int *rec_ix,
+                         const double *theta, const double *lo, const double *hi, double rel_step,
+                         double sigma, int nwin, const int *win_levels, double *H, double *H_rec);
+
 int ref_node_hessian(int nx, int nz, double h, double dt, int nsteps, const double *lam,
                      const double *mu, const double *nu, int nrec, const int *rec_ix,
                      const double *theta, const double *lo, const double *hi, double rel_step,
                      double sigma, int nwin, const int *win_levels, double *H, double *H_rec)
+{
+    return ref_node_hessian_stf(0, nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, theta, lo, hi,
+                                rel_step, sigma, nwin, win_levels, H, H_rec);
+}
+
+/* The same with the time function of the given kind (0 Gaussian, 1 Ricker). */
+int ref_node_hessian_stf(int kind, int nx, int nz, double h, double dt, int nsteps, const double *lam,
+                         const double *mu, const double *nu, int nrec, const int *rec_ix,
+                         const double *theta, const double *lo, const double *hi, double rel_step,
+                         double sigma, int nwin, const int *win_levels, double *H, double *H_rec)
 {
     size_t nrow = (size_t)(nsteps + 1) * nrec * 2;
     double *gall = malloc(sizeof(double) * nrow * 2 * NT);
@@ -501,7 +544,8 @@ int ref_node_hessian(int nx, int nz, double h, double dt, int nsteps, const doub
         double t[NT];
         for (int k = 0; k < NT; k++) t[k] = theta[k];
         t[j] += (q % 2 == 0) ? d : -d;
-        rc |= ref_forward(nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, t, gall + (size_t)q * nrow);
+        rc |= ref_forward_stf(kind, nx, nz, h, dt, nsteps, lam, mu, nu, nrec, rec_ix, t,
+                              gall + (size_t)q * nrow);
     }
     for (int j = 0; j < NT && rc == 0; j++) {
         double d = rel_step * (hi[j] - lo[j]);

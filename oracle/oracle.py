@@ -77,6 +77,12 @@ def lib():
         L.ref_scaled_logdet_sub.restype = c_int
         L.ref_dlmc.argtypes = [dp, dp, c_int, dp, c_int, c_int, c_double, dp, dp]
         L.ref_dlmc.restype = None
+        L.ref_ricker.argtypes = [c_double, c_double, c_double]
+        L.ref_ricker.restype = c_double
+        L.ref_forward_stf.argtypes = [c_int] + L.ref_forward.argtypes
+        L.ref_forward_stf.restype = c_int
+        L.ref_node_hessian_stf.argtypes = [c_int] + L.ref_node_hessian.argtypes
+        L.ref_node_hessian_stf.restype = c_int
         L.ref_delta_1d_dxs2.argtypes = [c_double, c_double, dp, dp]
         L.ref_delta_1d_dxs2.restype = None
         L.ref_stf_derivs.argtypes = [c_double, c_double, c_double, dp]
@@ -132,6 +138,14 @@ def delta_weights_dxs(alpha: float, h: float):
 def stf(t: float, ts: float, ws: float) -> float:
     """Gaussian source time function (Sec. 4.1) with omega_0 = omega_s."""
     return lib().ref_stf(float(t), float(ts), float(ws))
+
+
+def ricker(t: float, ts: float, f: float) -> float:
+    """Ricker wavelet (1 - 2a) exp(-a), a = (pi f (t - t_s))^2: the optional alternative time function."""
+    return lib().ref_ricker(float(t), float(ts), float(f))
+
+
+STF_GAUSS, STF_RICKER = 0, 1
 
 
 def source_patch(theta, nx: int, nz: int, h: float):
@@ -199,22 +213,22 @@ def step(grid: Grid, ux, uz, uxm, uzm, fx=None, fz=None):
     return uxn, uzn
 
 
-def forward(grid: Grid, theta):
-    """Seismograms g[m][r][c], m = 0..nsteps (Eq. forward_model)."""
+def forward(grid: Grid, theta, stf=STF_GAUSS):
+    """Seismograms g[m][r][c], m = 0..nsteps (Eq. forward_model); stf picks the time function."""
     g = np.zeros((grid.nsteps + 1, grid.nrec, 2))
-    rc = lib().ref_forward(*grid._args(), _pd(_d(theta)), _pd(g))
+    rc = lib().ref_forward_stf(int(stf), *grid._args(), _pd(_d(theta)), _pd(g))
     if rc != 0:
         raise ValueError("source patch leaves the grid interior")
     return g
 
 
-def node_hessian(grid: Grid, theta, lo, hi, rel_step, sigma, win_levels=None):
+def node_hessian(grid: Grid, theta, lo, hi, rel_step, sigma, win_levels=None, stf=STF_GAUSS):
     """(H[7][7], H_rec[nrec][nwin][7][7] or None): Gauss-Newton H_1 from central FD."""
     H = np.zeros(49)
     nwin = 0 if win_levels is None else len(win_levels)
     wl = _i(win_levels if win_levels is not None else [0])
     Hr = np.zeros(max(1, grid.nrec * nwin * 49))
-    rc = lib().ref_node_hessian(*grid._args(), _pd(_d(theta)), _pd(_d(lo)), _pd(_d(hi)),
+    rc = lib().ref_node_hessian_stf(int(stf), *grid._args(), _pd(_d(theta)), _pd(_d(lo)), _pd(_d(hi)),
                                 float(rel_step), float(sigma), nwin, _pi(wl), _pd(H),
                                 _pd(Hr) if nwin else ctypes.POINTER(ctypes.c_double)())
     if rc != 0:

@@ -794,3 +794,44 @@ def test_hessian_ii_equals_curvature_of_the_seismograms(adj_setup, oracle):
     e2 = np.max(np.abs(fd(1e-3) - H2) / sc)
     assert e1 < 1e-4 and e2 < e1 / 3.0
     assert np.max(np.abs(H2) / sc) > 1e-3   # the check is not vacuous
+
+
+# ------------------------------------------------------------------ Ricker time function
+def test_ricker_closed_forms(oracle):
+    """The optional Ricker wavelet: value 1 at t_s, zeros at |t - t_s| = 1/(pi f sqrt 2),
+    zero mean, and equal to minus the second time derivative of the paper's Gaussian
+    (omega_s = pi f sqrt 2) divided by its curvature 2 pi^2 f^2 and normalisation."""
+    ts, f = 0.21, 7.5
+    assert oracle.ricker(ts, ts, f) == 1.0
+    z = 1.0 / (math.pi * f * math.sqrt(2.0))
+    for s in (-1.0, 1.0):
+        assert abs(oracle.ricker(ts + s * z, ts, f)) < 1e-15
+        assert oracle.ricker(ts + s * 0.9 * z, ts, f) > 0 > oracle.ricker(ts + s * 1.1 * z, ts, f)
+    t = np.linspace(ts - 2.0, ts + 2.0, 40001)
+    r = np.array([oracle.ricker(x, ts, f) for x in t])
+    assert abs(np.trapezoid(r, t)) < 1e-12
+    ws = math.pi * f * math.sqrt(2.0)
+    for x in (ts - 0.13, ts - 0.02, ts + 0.05, ts + 0.31):
+        S_tt = oracle.stf_derivs(x, ts, ws)[3]
+        ref = -S_tt * math.sqrt(2.0 * math.pi) / ws / (2.0 * math.pi ** 2 * f * f)
+        assert abs(oracle.ricker(x, ts, f) - ref) < 1e-13
+
+
+def test_forward_with_either_time_function_is_the_forward_of_its_forcing(oracle):
+    """forward(theta, stf) equals the solve driven by the explicit forcing sequence
+    S(t_m) f_patch (Eq. source, the time function of the chosen kind), bit for bit."""
+    w = W.tiny(nx=40, nz=24, h=50.0, nsteps=60, nrec=3)
+    G = oracle.Grid.from_workload(w)
+    th = np.array([1010.0, 560.0, 0.12, 7.0, 5e13, 3e13, 7e13])
+    i0, j0, px, pz, ok = oracle.source_patch(th, w.nx, w.nz, w.h)
+    assert ok
+    for kind, fn in ((oracle.STF_GAUSS, oracle.stf), (oracle.STF_RICKER, oracle.ricker)):
+        f = np.zeros((w.nsteps, 2, w.nz, w.nx))
+        for m in range(w.nsteps):
+            s = fn(m * w.dt, th[2], th[3])
+            f[m, 0, j0:j0 + 6, i0:i0 + 6] = s * px
+            f[m, 1, j0:j0 + 6, i0:i0 + 6] = s * pz
+        g = oracle.forward(G, th, stf=kind)
+        assert np.max(np.abs(g)) > 0
+        assert np.array_equal(g, oracle.forward_field(G, f))
+    assert not np.allclose(oracle.forward(G, th, stf=oracle.STF_RICKER), oracle.forward(G, th))
