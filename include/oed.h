@@ -56,6 +56,11 @@ extern "C" {
 #define OED_JAC_SENSITIVITY 2 /* N_theta sensitivity solves per node driven by the
                                  analytic df/dtheta_j (Alg. 1 steps 1-5) */
 
+#define OED_STF_GAUSS 0  /* the paper's source time function (Sec. 4.1):
+                            S(t) = omega_s / sqrt(2 pi) exp(-omega_s^2 (t - t_s)^2 / 2) */
+#define OED_STF_RICKER 1 /* Ricker wavelet (1 - 2a) exp(-a), a = (pi f (t - t_s))^2, with the
+                            fourth source parameter read as the peak frequency f in Hz */
+
 #define OED_NTHETA 7
 #define OED_NH 28 /* unique entries of a symmetric 7x7 matrix, row-major upper triangle */
 
@@ -77,6 +82,11 @@ typedef struct {
     const int *rec_ix; /* [nrec] surface node index i of each receiver (0 <= i < nx);
                           repeats allowed */
     int precision;     /* OED_FP32 or OED_FP64 */
+    int stf;           /* source time function: OED_STF_GAUSS (0, the paper's) or
+                          OED_STF_RICKER.  The analytic derivatives of the time function
+                          (OED_JAC_SENSITIVITY, oed_hessian_ii, oed_hessian_map) exist
+                          for the Gaussian only: with OED_STF_RICKER those return
+                          OED_EINVAL.  Other values make the problem invalid. */
 } oed_problem;
 
 /* Create a context on the current CUDA device with device workspace for up to

@@ -22,6 +22,7 @@ OED_OK, OED_EINVAL, OED_ENOMEM, OED_ENOTPD, OED_ECUDA, OED_ETIMEOUT, OED_PENDING
 OED_SERVER_NO_AUTOTUNE = 1
 OED_FP32, OED_FP64 = 0, 1
 OED_JAC_PAIRS, OED_JAC_DIFFERENCE, OED_JAC_SENSITIVITY = 0, 1, 2
+OED_STF_GAUSS, OED_STF_RICKER = 0, 1
 NTHETA = 7
 
 SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
@@ -47,7 +48,7 @@ class Problem(ctypes.Structure):
                 ("z_top", ctypes.POINTER(ctypes.c_double)), ("vp", ctypes.POINTER(ctypes.c_double)),
                 ("vs", ctypes.POINTER(ctypes.c_double)), ("rho", ctypes.POINTER(ctypes.c_double)),
                 ("nrec", ctypes.c_int), ("rec_ix", ctypes.POINTER(ctypes.c_int)),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("stf", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -155,8 +156,9 @@ def _check(ctx_handle, rc: int, what: str):
         raise OedError(rc, f"{what}: {msg.decode() if msg else ''}")
 
 
-def make_problem(nx, nz, h, dt, nsteps, layers, rec_ix, precision=OED_FP32):
-    """Build an oed_problem (keeps the host arrays alive on the returned object)."""
+def make_problem(nx, nz, h, dt, nsteps, layers, rec_ix, precision=OED_FP32, stf=None):
+    """Build an oed_problem (keeps the host arrays alive on the returned object);
+    stf: OED_STF_GAUSS (default) or OED_STF_RICKER."""
     p = Problem()
     p.nx, p.nz, p.h, p.dt, p.nsteps = int(nx), int(nz), float(h), float(dt), int(nsteps)
     p.nlayers = len(layers)
@@ -169,12 +171,13 @@ def make_problem(nx, nz, h, dt, nsteps, layers, rec_ix, precision=OED_FP32):
     p._rec = (ctypes.c_int * len(rec_ix))(*[int(r) for r in rec_ix])
     p.rec_ix = p._rec
     p.precision = int(precision)
+    p.stf = OED_STF_GAUSS if stf is None else int(stf)
     return p
 
 
-def problem_from_workload(w, precision=OED_FP32, rec_ix=None, nsteps=None):
+def problem_from_workload(w, precision=OED_FP32, rec_ix=None, nsteps=None, stf=None):
     return make_problem(w.nx, w.nz, w.h, w.dt, w.nsteps if nsteps is None else nsteps, w.layers,
-                        w.rec_ix if rec_ix is None else rec_ix, precision)
+                        w.rec_ix if rec_ix is None else rec_ix, precision, stf)
 
 
 def oed_workspace_bytes(problem: Problem, max_solves: int) -> int:

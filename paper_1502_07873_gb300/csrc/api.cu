@@ -54,6 +54,7 @@ static bool problem_ok(const oed_problem *p, std::string *why)
     for (int r = 0; r < p->nrec; r++)
         if (p->rec_ix[r] < 0 || p->rec_ix[r] >= p->nx) return fail("receiver index outside 0..nx-1");
     if (p->precision != OED_FP32 && p->precision != OED_FP64) return fail("precision must be OED_FP32 or OED_FP64");
+    if (p->stf != OED_STF_GAUSS && p->stf != OED_STF_RICKER) return fail("stf must be OED_STF_GAUSS or OED_STF_RICKER");
     return true;
 }
 
@@ -182,6 +183,7 @@ int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
     if (!ctx) return OED_ENOMEM;
     ctx->g = make_geometry(p);
     ctx->precision = p->precision;
+    ctx->stf = p->stf;
     ctx->elem = p->precision == OED_FP64 ? 8 : 4;
     ctx->max_solves = max_solves;
     cudaGetDevice(&ctx->device);
@@ -401,6 +403,8 @@ int oed_set_jacobian(oed_ctx *ctx, int mode)
     if (!ctx) return OED_EINVAL;
     if (mode != OED_JAC_PAIRS && mode != OED_JAC_DIFFERENCE && mode != OED_JAC_SENSITIVITY)
         return set_err(ctx, OED_EINVAL, "oed_set_jacobian: unknown Jacobian form");
+    if (mode == OED_JAC_SENSITIVITY && ctx->stf != OED_STF_GAUSS)
+        return set_err(ctx, OED_EINVAL, "oed_set_jacobian: sensitivity solves need the Gaussian time function");
     ctx->jac_mode = mode;
     return OED_OK;
 }
@@ -493,6 +497,8 @@ int oed_hessian_ii(oed_ctx *ctx, const double *theta, int n, const double *y, do
         return set_err(ctx, OED_EINVAL, "oed_hessian_ii: bad pointer arguments");
     if (!(sigma > 0) || !std::isfinite(sigma)) return set_err(ctx, OED_EINVAL, "oed_hessian_ii: sigma must be positive");
     if (ctx->g.nrec > kMaxRecHessian) return set_err(ctx, OED_EINVAL, "oed_hessian_ii: at most 256 receivers");
+    if (ctx->stf != OED_STF_GAUSS)
+        return set_err(ctx, OED_EINVAL, "oed_hessian_ii: the dual solve needs the Gaussian time function");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t per = (size_t)ctx->g.nlev * ctx->g.nrec * 2;
     const int chunk = ctx->max_solves;
@@ -549,6 +555,8 @@ int oed_hessian_map(oed_ctx *ctx, double *theta, int n, const double *y, const d
     if (ctx && (param_mask < 1 || param_mask > 127))
         return set_err(ctx, OED_EINVAL, "oed_hessian_map: param_mask must be in 1..127");
     if (!ctx) return OED_EINVAL;
+    if (ctx->stf != OED_STF_GAUSS)
+        return set_err(ctx, OED_EINVAL, "oed_hessian_map: the dual solve needs the Gaussian time function");
     if (iters < 0 || iters > 100) return set_err(ctx, OED_EINVAL, "oed_hessian_map: iters must be in 0..100");
     if (n < 0 || (n > 0 && (!theta || !y || !H || !grad))) return set_err(ctx, OED_EINVAL, "oed_hessian_map: bad pointers");
     for (int it = 0; it <= iters; it++) {

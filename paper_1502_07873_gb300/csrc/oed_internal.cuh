@@ -96,6 +96,7 @@ struct StepTuning {
 struct oed_ctx {
     oed::Geometry g;
     int precision;
+    int stf = OED_STF_GAUSS;   // source time function of the problem
     int max_solves;
     int device;
     size_t elem;               // 4 or 8

@@ -189,6 +189,7 @@ size_t oed_server_request_bytes(const oed_request *req, int chunk_nodes)
     if (!req || req->n < 1 || chunk_nodes < 1) return 0;
     const int per_node = req->jacobian == OED_JAC_PAIRS ? 15 : 7;
     const int chunk = req->n < chunk_nodes ? req->n : chunk_nodes;
+    if (req->jacobian == OED_JAC_SENSITIVITY && req->problem.stf != OED_STF_GAUSS) return 0;
     const size_t ws = oed_workspace_bytes(&req->problem, per_node * chunk);
     if (!ws) return 0;
     return ws + (size_t)req->n * (7 + 1 + 49) * sizeof(double) + 4096;

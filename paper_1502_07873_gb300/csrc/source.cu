@@ -105,9 +105,16 @@ __device__ bool source_patch6(const double *th, double h, int *kx, int *kz, doub
     return true;
 }
 
-__device__ __forceinline__ double stf_value(double t, double ts, double ws)
+// S(t) of the given kind: OED_STF_GAUSS (Sec. 4.1, w = omega_s) or OED_STF_RICKER
+// ((1 - 2a) e^{-a}, a = (pi w (t - ts))^2, w the peak frequency)
+__device__ __forceinline__ double stf_value(int kind, double t, double ts, double ws)
 {
     const double u = t - ts;
+    if (kind == OED_STF_RICKER) {
+        double a = 3.141592653589793 * ws * u;
+        a = a * a;
+        return (1.0 - 2.0 * a) * exp(-a);
+    }
     return ws * 0.3989422804014327 * exp(-0.5 * ws * ws * u * u);   // w / sqrt(2 pi) e^{...}
 }
 
@@ -120,7 +127,7 @@ __device__ __forceinline__ double stf_value(double t, double ts, double ws)
 // on their 7x7 union); for j = t_s, omega_s the time function differs.
 template <typename real>
 __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, int per_node, int sens,
-                          FdStep step, Geometry g, const RowCoef<real> *__restrict__ rows,
+                          int stf_kind, FdStep step, Geometry g, const RowCoef<real> *__restrict__ rows,
                           SourceDesc<real> *__restrict__ src, real *__restrict__ stf,
                           double *__restrict__ theta_out)
 {
@@ -239,8 +246,9 @@ __global__ void k_sources(const double *__restrict__ theta_nodes, int nsolve, in
     }
     for (int m = threadIdx.x; m < g.nsteps; m += blockDim.x) {
         const double t = m * g.dt;
-        double v = time_diff ? stf_value(t, tp[2], tp[3]) - stf_value(t, tm[2], tm[3])
-                             : stf_value(t, th[2], th[3]);
+        double v = time_diff ? stf_value(stf_kind, t, tp[2], tp[3]) - stf_value(stf_kind, t, tm[2], tm[3])
+                             : stf_value(stf_kind, t, th[2], th[3]);
+        // (sensitivity solves: Gaussian only, the host refuses them for any other kind)
         if (time_kind == 1) v *= th[3] * th[3] * (t - th[2]);                 // dS/dt_s
         if (time_kind == 2) v *= 1.0 / th[3] - th[3] * (t - th[2]) * (t - th[2]);   // dS/domega_s
         stf[(size_t)s * g.nsteps + m] = (real)v;
@@ -472,11 +480,11 @@ void launch_sources(const oed_ctx *ctx, const double *theta_nodes, int nnode, in
     if (nsolve <= 0) return;
     if (ctx->precision == OED_FP64)
         k_sources<double><<<nsolve, 128, 0, s>>>(
-            theta_nodes, nsolve, per_node, sens, st, ctx->g, (const RowCoef<double> *)ctx->d_rows,
+            theta_nodes, nsolve, per_node, sens, ctx->stf, st, ctx->g, (const RowCoef<double> *)ctx->d_rows,
             (SourceDesc<double> *)ctx->d_src, (double *)ctx->d_stf, ctx->d_theta);
     else
         k_sources<float><<<nsolve, 128, 0, s>>>(
-            theta_nodes, nsolve, per_node, sens, st, ctx->g, (const RowCoef<float> *)ctx->d_rows,
+            theta_nodes, nsolve, per_node, sens, ctx->stf, st, ctx->g, (const RowCoef<float> *)ctx->d_rows,
             (SourceDesc<float> *)ctx->d_src, (float *)ctx->d_stf, ctx->d_theta);
 }
 

@@ -97,3 +97,23 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.replace("the oracle", ""), f
+
+
+def test_time_function_kind_is_validated_on_the_host(P):
+    """stf must be Gaussian or Ricker; the server refuses sensitivity solves with a Ricker
+    source at submission (request bytes 0), before any device work."""
+    w = W.batched()
+    gauss = P.oed_workspace_bytes(P.problem_from_workload(w), 100)
+    assert gauss > 0
+    assert P.oed_workspace_bytes(P.problem_from_workload(w, stf=P.OED_STF_RICKER), 100) == gauss
+    assert P.oed_workspace_bytes(P.problem_from_workload(w, stf=2), 100) == 0
+    assert P.oed_workspace_bytes(P.problem_from_workload(w, stf=-1), 100) == 0
+    L = P.library()
+    p = P.problem_from_workload(w, stf=P.OED_STF_RICKER)
+    th = np.tile(np.array(w.prior_lo) * 0.5 + np.array(w.prior_hi) * 0.5, (4, 1))
+    sizes = {}
+    for jac in (P.OED_JAC_PAIRS, P.OED_JAC_DIFFERENCE, P.OED_JAC_SENSITIVITY):
+        req = P.make_request(p, th, np.full(4, 0.25), w.prior_lo, w.prior_hi, w.rel_step, 0.1, jac)
+        sizes[jac] = L.oed_server_request_bytes(ctypes.byref(req), 16)
+    assert sizes[P.OED_JAC_PAIRS] > sizes[P.OED_JAC_DIFFERENCE] > 0
+    assert sizes[P.OED_JAC_SENSITIVITY] == 0
