@@ -28,6 +28,8 @@
 // patch nodes.  HBM traffic is only the seismogram samples and the source time
 // function: the wavefield never leaves the chip, so this kernel is bound by
 // instruction issue, shared-memory latency and the per-step barrier, not by HBM.
+#include <type_traits>
+
 #include "stencil_cell.cuh"
 
 namespace oed {
@@ -153,6 +155,9 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     const bool scolB = c + 1 < g.nx && (unsigned)siB < (unsigned)kPatch;
     const float *stf = a.stf + (size_t)s * g.nsteps;
     float *trace = a.trace + (size_t)s * g.nlev * g.nrec * 2;
+    // the warps that hold a side column run the march with the absorbing patch, the
+    // others (most of them) a march without it
+    const bool warp_side = __any_sync(0xffffffffu, active && kind != 0);
     cluster_barrier();
 
     for (int m = 0; m < g.nsteps; m++) {
@@ -203,34 +208,45 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 float2 pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
                 float2 pe = *reinterpret_cast<const float2 *>(&sp[1].x);
                 int left = lstop - l;   // rows of the march still to do, this one included
-                auto row = [&](const Row2 &wn, Row2 &wc, Row2 &ws) {
-                    row_from(pw, pm, pe, ws);
-                    float4 u = pu;
-                    if (--left > 0) {
-                        sp += sq;
-                        pm = sp[0];
-                        pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
-                        pe = *reinterpret_cast<const float2 *>(&sp[1].x);
-                        pu = o[sq];
+                // side: the warp holds a side column (absorbing patch compiled in)
+                auto march = [&](auto side) {
+                    auto row = [&](const Row2 &wn, Row2 &wc, Row2 &ws) {
+                        row_from(pw, pm, pe, ws);
+                        float4 u = pu;
+                        if (--left > 0) {
+                            sp += sq;
+                            pm = sp[0];
+                            pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
+                            pe = *reinterpret_cast<const float2 *>(&sp[1].x);
+                            pu = o[sq];
+                        }
+                        south(wc, ws);
+                        const FacCoef<float> K = *cf;
+                        pair_update(K, wn, wc, ws, u);
+                        if constexpr (decltype(side)::value) {
+                            if (kind) absorbing(K.cp, K.cs, u, wc, false, kind, u);
+                        }
+                        *o = u;
+                        o += sq;
+                        cf++;
+                    };
+                    for (; l + 3 <= lstop; l += 3) {
+                        row(rn, rc, rs);   // window (n, c, s)
+                        row(rc, rs, rn);   // row l+2 lands in rn
+                        row(rs, rn, rc);   // row l+3 lands in rc
                     }
-                    south(wc, ws);
-                    const FacCoef<float> K = *cf;
-                    pair_update(K, wn, wc, ws, u);
-                    if (kind) absorbing(K.cp, K.cs, u, wc, false, kind, u);
-                    *o = u;
-                    o += sq;
-                    cf++;
+                    for (; l < lstop; l++) {
+                        row(rn, rc, rs);
+                        rn = rc;
+                        rc = rs;
+                    }
                 };
-                for (; l + 3 <= lstop; l += 3) {
-                    row(rn, rc, rs);   // window (n, c, s)
-                    row(rc, rs, rn);   // row l+2 lands in rn
-                    row(rs, rn, rc);   // row l+3 lands in rc
-                }
-                for (; l < lstop; l++) {
-                    row(rn, rc, rs);
-                    rn = rc;
-                    rc = rs;
-                }
+                // a warp-uniform choice: a branch inside the march body would split the
+                // unrolled rows into separate blocks and cost the scheduler its overlap
+                if (warp_side)
+                    march(std::true_type{});
+                else
+                    march(std::false_type{});
             }
             // what is left: a last interior row whose south neighbour sits in CTA rank+1,
             // or the absorbing bottom row
