@@ -207,13 +207,13 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 float4 pm = sp[0], pu = o[0];
                 float2 pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
                 float2 pe = *reinterpret_cast<const float2 *>(&sp[1].x);
-                int left = lstop - l;   // rows of the march still to do, this one included
-                // side: the warp holds a side column (absorbing patch compiled in)
+                // side: the warp holds a side column (absorbing patch compiled in);
+                // pf: a row below the south row exists, prefetch it (every row but the last)
                 auto march = [&](auto side) {
-                    auto row = [&](const Row2 &wn, Row2 &wc, Row2 &ws) {
+                    auto row = [&](auto pf, const Row2 &wn, Row2 &wc, Row2 &ws) {
                         row_from(pw, pm, pe, ws);
                         float4 u = pu;
-                        if (--left > 0) {
+                        if constexpr (decltype(pf)::value) {
                             sp += sq;
                             pm = sp[0];
                             pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
@@ -230,16 +230,32 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                         o += sq;
                         cf++;
                     };
-                    for (; l + 3 <= lstop; l += 3) {
-                        row(rn, rc, rs);   // window (n, c, s)
-                        row(rc, rs, rn);   // row l+2 lands in rn
-                        row(rs, rn, rc);   // row l+3 lands in rc
+                    const std::true_type P{};
+                    const std::false_type N{};
+                    for (; l + 3 < lstop; l += 3) {
+                        row(P, rn, rc, rs);   // window (n, c, s)
+                        row(P, rc, rs, rn);   // row l+2 lands in rn
+                        row(P, rs, rn, rc);   // row l+3 lands in rc
                     }
-                    for (; l < lstop; l++) {
-                        row(rn, rc, rs);
+                    // one to three rows left, the last without prefetch; the window ends
+                    // as (rn, rc) = (north, centre) of the row after the march
+                    const int r = lstop - l;
+                    if (r == 3) {
+                        row(P, rn, rc, rs);
+                        row(P, rc, rs, rn);
+                        row(N, rs, rn, rc);
+                    } else if (r == 2) {
+                        row(P, rn, rc, rs);
+                        row(N, rc, rs, rn);
+                        const Row2 t = rn;
+                        rn = rs;
+                        rc = t;
+                    } else {
+                        row(N, rn, rc, rs);
                         rn = rc;
                         rc = rs;
                     }
+                    l = lstop;
                 };
                 // a warp-uniform choice: a branch inside the march body would split the
                 // unrolled rows into separate blocks and cost the scheduler its overlap
