@@ -4,7 +4,7 @@
 //
 // CTA r of a cluster of C owns rows [r R, min((r+1) R, nz)) of the grid, both
 // components and both time levels, in its shared memory:
-//     A, B : [R][npair + 2] float4,   coef : [R] FacCoef,   the solve's 2 x 49
+//     A, B : [R][npair + 2] float4,   coef : [R] KP (FacCoef in (x, z) pairs),   the solve's 2 x 49
 //     source weights (kept on chip: read from global memory every step they put an L1
 //     round trip on the critical path of the warps that own the patch columns)
 // Slot q of a row holds the column pair p = q - 1 as (x_2p, z_2p, x_2p+1, z_2p+1);
@@ -97,19 +97,123 @@ __device__ __forceinline__ float2 ld_cluster2(unsigned addr)
     return v;
 }
 
+// ------------------------------------------------------------------------------
+// The node update of stencil_cell.cuh on packed FP32 pairs.  A column's two
+// components (x, z) sit side by side in a slot, and the update of u_x and of u_z
+// runs through the same sequence of operations with their own coefficients, so
+// each step of it is one two-wide instruction (fma/mul/add .f32x2, rounded per
+// component exactly like the scalar fmaf/fmul/fadd).  Every value is computed by
+// the same operations in the same order as pair_update, so the bits are those of
+// the streaming kernels.
+
+// a row's coefficients as (x, z) pairs: operator term A = a*lap + vs*dv_s +
+// vn*dv_n + ds*d_s + dn*d_n, and the absorbing speeds (c_p, c_s) dt/h
+struct __align__(16) KP {
+    float2 a, vs, vn, ds, dn, c, pad0, pad1;
+};
+
+__device__ __forceinline__ KP pack_coef(const FacCoef<float> &f)
+{
+    KP k;
+    k.a = make_float2(f.axx, f.azx);
+    k.vs = make_float2(f.axzp, f.azzp);
+    k.vn = make_float2(f.naxzm, f.nazzm);
+    k.ds = make_float2(f.px, f.pz);
+    k.dn = make_float2(f.nqx, f.nqz);
+    k.c = make_float2(f.cp, f.cs);
+    k.pad0 = k.pad1 = make_float2(0.0f, 0.0f);
+    return k;
+}
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as one rounding: b * (-1) is exact, so fma(b, -1, a) rounds a - b once
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+// Row2 with each quantity as a (x, z) pair per column a = c, b = c+1; the east - west
+// differences, which enter the other component's update, are stored swapped (z, x)
+struct Row2P {
+    float2 ca, cb;   // centre values
+    float2 la, lb;   // (e - c) - (c - w)
+    float2 da, db;   // (dz, dx): east - west differences, swapped
+    float2 va, vb;   // south row minus this row
+};
+
+__device__ __forceinline__ void row_fromP(float2 w, float4 m, float2 e, Row2P &r)
+{
+    r.ca = make_float2(m.x, m.y);
+    r.cb = make_float2(m.z, m.w);
+    const float2 t = sub2(r.cb, r.ca);
+    r.la = sub2(t, sub2(r.ca, w));
+    r.lb = sub2(sub2(e, r.cb), t);
+    r.da = make_float2(m.w - w.y, m.z - w.x);
+    r.db = make_float2(e.y - m.y, e.x - m.x);
+}
+
+__device__ __forceinline__ void southP(Row2P &c, const Row2P &s)
+{
+    c.va = sub2(s.ca, c.ca);
+    c.vb = sub2(s.cb, c.cb);
+}
+
+// u^{m+1} of the pair (u holds u^{m-1} on entry, slot order x_a, z_a, x_b, z_b)
+__device__ __forceinline__ void pair_updateP(const KP &K, const Row2P &n, const Row2P &c, const Row2P &s,
+                                             float4 &u)
+{
+    float2 A = __fmul2_rn(K.a, c.la);
+    A = fma2(K.vs, c.va, A);
+    A = fma2(K.vn, n.va, A);
+    A = fma2(K.ds, s.da, A);
+    A = fma2(K.dn, n.da, A);
+    float2 B = __fmul2_rn(K.a, c.lb);
+    B = fma2(K.vs, c.vb, B);
+    B = fma2(K.vn, n.vb, B);
+    B = fma2(K.ds, s.db, B);
+    B = fma2(K.dn, n.db, B);
+    const float2 xa = add2(c.ca, add2(sub2(c.ca, make_float2(u.x, u.y)), A));
+    const float2 xb = add2(c.cb, add2(sub2(c.cb, make_float2(u.z, u.w)), B));
+    u = make_float4(xa.x, xa.y, xb.x, xb.y);
+}
+
+// the absorbing rows and side columns of stencil_cell.cuh's absorbing()
+__device__ __forceinline__ void absorbingP(float2 cpcs, float4 nv, const Row2P &c, bool bottom, int kind, float4 &u)
+{
+    const float cp = cpcs.x, cs = cpcs.y;
+    if (bottom) {
+        u.x = absorb(c.ca.x, nv.x, cs);
+        u.z = absorb(c.cb.x, nv.z, cs);
+        u.y = absorb(c.ca.y, nv.y, cp);
+        u.w = absorb(c.cb.y, nv.w, cp);
+    }
+    if (kind & 1) {
+        u.x = absorb(c.ca.x, c.cb.x, cp);
+        u.y = absorb(c.ca.y, c.cb.y, cs);
+    }
+    if (kind & 2) {
+        u.z = absorb(c.cb.x, c.ca.x, cp);
+        u.w = absorb(c.cb.y, c.ca.y, cs);
+    }
+    if (kind & 4) {   // column nx-1: its east - west difference is -west (the ghost east is 0)
+        u.x = absorb(c.ca.x, -c.da.y, cp);
+        u.y = absorb(c.ca.y, -c.da.x, cs);
+        u.z = 0.0f;
+        u.w = 0.0f;
+    }
+}
+
 // q points at the thread's own slot of a local row
-__device__ __forceinline__ void load_row(const float4 *q, Row2 &r)
+__device__ __forceinline__ void load_row(const float4 *q, Row2P &r)
 {
     const float2 w = *reinterpret_cast<const float2 *>(&q[-1].z);
     const float2 e = *reinterpret_cast<const float2 *>(&q[1].x);
-    row_from(w, *q, e, r);
+    row_fromP(w, *q, e, r);
 }
 
 // the same slot of a row in CTA `nb` of the cluster
-__device__ __forceinline__ void load_row_remote(const float4 *q, unsigned nb, Row2 &r)
+__device__ __forceinline__ void load_row_remote(const float4 *q, unsigned nb, Row2P &r)
 {
     const unsigned b = remote_addr(smem_addr(q), nb);
-    row_from(ld_cluster2(b - 8u), ld_cluster4(b), ld_cluster2(b + 16u), r);
+    row_fromP(ld_cluster2(b - 8u), ld_cluster4(b), ld_cluster2(b + 16u), r);
 }
 
 // float offset of node (column i, component comp) within a shared row
@@ -129,12 +233,12 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     const int nrows = max(0, min(R, g.nz - j0));
     const int lvl = R * sq;   // float4 slots per level
     float4 *A = smem4, *B = smem4 + lvl;
-    FacCoef<float> *coef = reinterpret_cast<FacCoef<float> *>(smem4 + 2 * lvl);
+    KP *coef = reinterpret_cast<KP *>(smem4 + 2 * lvl);
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
 
     for (int k = tid; k < 2 * lvl; k += nthr) smem4[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int k = tid; k < nrows; k += nthr) coef[k] = a.fac[j0 + k];
+    for (int k = tid; k < nrows; k += nthr) coef[k] = pack_coef(a.fac[j0 + k]);
     float *sw = reinterpret_cast<float *>(coef + R);   // this solve's source weights, x then z
     for (int k = tid; k < 2 * kPatch * kPatch; k += nthr)
         sw[k] = k < kPatch * kPatch ? a.src[blockIdx.y].wx[k] : a.src[blockIdx.y].wz[k - kPatch * kPatch];
@@ -169,7 +273,7 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 trace[(size_t)m * g.nrec * 2 + q] = row0[node_off(a.rec[q >> 1], q & 1)];
         }
         if (active && l0 < l1) {
-            Row2 rn, rc, rs;
+            Row2P rn, rc, rs;
             int l = l0;
             load_row(cur + l * sq, rc);
             if (top) {   // surface row: no north differences, cross terms on the row itself
@@ -177,14 +281,14 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                     load_row(cur + (l + 1) * sq, rs);
                 else   // a one-row slab
                     load_row_remote(cur, rank + 1, rs);
-                south(rc, rs);
-                Row2 nt = rc;
-                nt.vxa = nt.vxb = nt.vza = nt.vzb = 0.0f;
+                southP(rc, rs);
+                Row2P nt = rc;
+                nt.va = nt.vb = make_float2(0.0f, 0.0f);
                 float4 *o = nxt + l * sq;
                 float4 u = *o;
-                const FacCoef<float> K = coef[l];
-                pair_update(K, nt, rc, rs, u);
-                if (kind) absorbing(K.cp, K.cs, u, rc, false, kind, u);
+                const KP K = coef[l];
+                pair_updateP(K, nt, rc, rs, u);
+                if (kind) absorbingP(K.c, u, rc, false, kind, u);
                 *o = u;
                 rn = rc;
                 rc = rs;
@@ -194,7 +298,7 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                     load_row(cur + (l - 1) * sq, rn);
                 else
                     load_row_remote(cur + (R - 1) * sq, rank - 1, rn);
-                south(rn, rc);
+                southP(rn, rc);
             }
             // rows whose south neighbour is a local row and that are not the bottom row:
             // unrolled by three with the three window rows taking turns
@@ -203,15 +307,15 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 // the loads of the next row are issued before the update of this one
                 const float4 *sp = cur + (l + 1) * sq;
                 float4 *o = nxt + l * sq;
-                const FacCoef<float> *cf = coef + l;
+                const KP *cf = coef + l;
                 float4 pm = sp[0], pu = o[0];
                 float2 pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
                 float2 pe = *reinterpret_cast<const float2 *>(&sp[1].x);
                 // side: the warp holds a side column (absorbing patch compiled in);
                 // pf: a row below the south row exists, prefetch it (every row but the last)
                 auto march = [&](auto side) {
-                    auto row = [&](auto pf, const Row2 &wn, Row2 &wc, Row2 &ws) {
-                        row_from(pw, pm, pe, ws);
+                    auto row = [&](auto pf, const Row2P &wn, Row2P &wc, Row2P &ws) {
+                        row_fromP(pw, pm, pe, ws);
                         float4 u = pu;
                         if constexpr (decltype(pf)::value) {
                             sp += sq;
@@ -220,11 +324,11 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                             pe = *reinterpret_cast<const float2 *>(&sp[1].x);
                             pu = o[sq];
                         }
-                        south(wc, ws);
-                        const FacCoef<float> K = *cf;
-                        pair_update(K, wn, wc, ws, u);
+                        southP(wc, ws);
+                        const KP K = *cf;
+                        pair_updateP(K, wn, wc, ws, u);
                         if constexpr (decltype(side)::value) {
-                            if (kind) absorbing(K.cp, K.cs, u, wc, false, kind, u);
+                            if (kind) absorbingP(K.c, u, wc, false, kind, u);
                         }
                         *o = u;
                         o += sq;
@@ -247,7 +351,7 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                     } else if (r == 2) {
                         row(P, rn, rc, rs);
                         row(N, rc, rs, rn);
-                        const Row2 t = rn;
+                        const Row2P t = rn;
                         rn = rs;
                         rc = t;
                     } else {
@@ -267,18 +371,18 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
             // what is left: a last interior row whose south neighbour sits in CTA rank+1,
             // or the absorbing bottom row
             for (; l < l1; l++) {
-                const FacCoef<float> K = coef[l];
+                const KP K = coef[l];
                 float4 *o = nxt + l * sq;
                 float4 u = *o;
                 if (j0 + l == g.nz - 1) {
                     const float4 nv = l > 0 ? cur[(l - 1) * sq]
                                             : ld_cluster4(remote_addr(smem_addr(cur + (R - 1) * sq), rank - 1));
-                    absorbing(K.cp, K.cs, nv, rc, true, kind, u);
+                    absorbingP(K.c, nv, rc, true, kind, u);
                 } else {
                     load_row_remote(cur, rank + 1, rs);
-                    south(rc, rs);
-                    pair_update(K, rn, rc, rs, u);
-                    if (kind) absorbing(K.cp, K.cs, u, rc, false, kind, u);
+                    southP(rc, rs);
+                    pair_updateP(K, rn, rc, rs, u);
+                    if (kind) absorbingP(K.c, u, rc, false, kind, u);
                 }
                 *o = u;
                 rn = rc;
@@ -330,7 +434,7 @@ static ResShape resident_shape(const Geometry &g, int C)
     const int R = (g.nz + C - 1) / C;
     if ((C - 1) * R >= g.nz) return r;   // a CTA would own no rows
     const int sq = npair + 2;   // ghost slots on both sides
-    const size_t smem = (size_t)2 * R * sq * sizeof(float4) + (size_t)R * sizeof(FacCoef<float>) +
+    const size_t smem = (size_t)2 * R * sq * sizeof(float4) + (size_t)R * sizeof(KP) +
                         2 * kPatch * kPatch * sizeof(float);
     if (smem > 227 * 1024) return r;
     int nseg = kResThreads / npair;
