@@ -38,7 +38,8 @@ BYTES_PER_CELL_UPDATE = {"f32": 24, "f64": 48}   # read u^m, u^{m-1}; write u^{m
 # vertical and cross differences 1 + 1 (each shared with the next row), the operator
 # term 1 multiply + 4 multiply-adds = 9, the leap-frog increment form 3
 FLOPS_PER_CELL_UPDATE = 33
-# FP32 instructions behind those flops (the FP32 pipe's own roofline: 25 per node)
+# FP32 lane operations behind those flops (the FP32 pipe's own roofline: 25 per node; a
+# packed two-wide instruction counts as two, one per lane it occupies)
 FP32_INSTR_PER_CELL_UPDATE = 25
 # FP32 peak derived from the unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 (FMA)
 # x 2.07 GHz maximum SM clock
