@@ -17,6 +17,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -128,11 +129,21 @@ KERNEL_SOURCES = {"k_resident": ("resident.cu", "stencil_cell.cuh", "oed_interna
                   "k_step_tma": ("stream_tma.cu", "stencil_cell.cuh", "oed_internal.cuh")}
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace collapsed (string literals in
+    these kernels hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_sources_hash(kernel: str) -> str:
+    """Hash of a stencil kernel's code (comments and layout ignored): a committed ncu
+    traffic figure is used only while the code it was taken on is unchanged."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_1502_07873_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1502_07873_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

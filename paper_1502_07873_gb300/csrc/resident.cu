@@ -23,20 +23,24 @@
 // east - west differences are formed; its south differences are formed when the
 // next row arrives, and all of them serve it again as the centre and north row.
 // The surface row, the bottom row and the rows whose neighbour lives in another
-// CTA are peeled off the main loop; the absorbing side columns are patched by the
-// threads that own them; the source term is added after the sweep to the few
-// patch nodes.  HBM traffic is only the seismogram samples and the source time
-// function: the wavefield never leaves the chip, so this kernel is bound by
-// instruction issue, shared-memory latency and the per-step barrier, not by HBM.
+// CTA are peeled off the main loop, and so are the march's last one to three rows
+// (the only ones that do not prefetch): the unrolled march body has no branch.  The
+// absorbing side columns are patched by the threads that own them, in a second
+// compiled march that only the warps holding a side column run; the source term
+// is added after the sweep to the few patch nodes.  The arithmetic runs on packed
+// (x, z) pairs (.f32x2).  HBM traffic is only the seismogram samples and the source
+// time function: the wavefield never leaves the chip, so this kernel is bound by
+// shared-memory latency and throughput and the per-step barrier, not by HBM.
 #include <type_traits>
 
 #include "stencil_cell.cuh"
 
 namespace oed {
 
-// Block size and register budget: registers are split over the SM's four
-// schedulers (16 K each), so 20 warps of 96 registers is the most one CTA can hold
-// with the row window in registers.
+// Block size and register cap: registers are split over the SM's four schedulers
+// (16 K each), so 20 warps of 96 registers is the most one CTA can hold (the packed
+// update needs 80).  Three row segments of about twelve rows per column pair (19
+// warps at 401 columns) measured faster than one, two, four or five.
 constexpr int kResThreads = 640;
 constexpr int kResRegs = 96;
 
