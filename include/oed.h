@@ -133,6 +133,17 @@ int oed_last_step_time(const oed_ctx *ctx, float *ms, int *launches);
  * 15 * oed_chunk_nodes(ctx). */
 int oed_autotune(oed_ctx *ctx, int nsolve, void *stream);
 
+/* Failure-detection self-test of the bounded waits.  Every wait in the library's
+ * kernels on another agent's progress (the TMA kernel's mbarrier waits) gives up
+ * after a time limit (2 s), raises the context's device flag, lets its copies in
+ * flight land and returns; the flag turns the affected nodes' status into
+ * OED_ETIMEOUT and is cleared before the next time loop, so the context stays usable.
+ * This call launches one CTA that waits, with a limit of `seconds` (0 < seconds <= 2),
+ * for a barrier phase nothing completes, and reads the flag back after synchronising
+ * the stream.  Returns OED_ETIMEOUT when the wait expired and the flag arrived (the
+ * expected outcome), OED_ECUDA otherwise, OED_EINVAL for a bad argument. */
+int oed_wait_selftest(oed_ctx *ctx, double seconds, void *stream);
+
 /* Current / forced choice: cluster_size 0 = streaming kernel with the given
  * rows_per_thread (2, 4, 8) and warps_per_block (1, 2, 4, 8); cluster_size > 0 =
  * cluster-resident kernel (OED_EINVAL if the grid does not fit). */

@@ -33,7 +33,7 @@ SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_gauss_newton_noalloc", "oed_server_create", "oed_server_request_bytes",
            "oed_server_submit", "oed_server_poll", "oed_server_wait", "oed_server_stats",
            "oed_server_destroy", "oed_eig_subset", "oed_dlmc", "oed_hessian_ii", "oed_newton_step",
-           "oed_hessian_map")
+           "oed_hessian_map", "oed_wait_selftest")
 
 
 class OedError(RuntimeError):
@@ -103,6 +103,7 @@ def library():
         "oed_set_tuning": (i, [vp, i, i, i]),
         "oed_resident_min_cluster": (i, [vp]),
         "oed_set_jacobian": (i, [vp, i]),
+        "oed_wait_selftest": (i, [vp, d, vp]),
         "oed_get_jacobian": (i, [vp]),
         "oed_gauss_newton_noalloc": (i, [vp, i, i, i, i, dp, dp, d, d, vp, vp]),
         "oed_server_create": (i, [ctypes.POINTER(vp), sz, i, i, i]),
@@ -303,6 +304,11 @@ def oed_eig_subset(ctx: Optional[Context], H, w, lo, hi, free, eig, dkl=None, st
                                   _ptr(dkl), _ptr(status), _ptr(n_bad), _stream(stream))
     _check(h, rc, "oed_eig_subset")
     return eig
+
+
+def oed_wait_selftest(ctx: Context, seconds: float = 0.05, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status code (OED_ETIMEOUT expected)."""
+    return int(library().oed_wait_selftest(ctx.handle, float(seconds), _stream(stream)))
 
 
 def oed_hessian_ii(ctx: Context, theta, y, sigma: float, H, grad=None, status=None, stream=None):

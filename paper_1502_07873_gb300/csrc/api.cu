@@ -109,6 +109,9 @@ static void drop_graphs(oed_ctx *ctx)
 // (built on first use for this batch size).
 static int run_steps(oed_ctx *ctx, int nsolve, cudaStream_t st)
 {
+    // the expiry flag describes this time loop only
+    cudaError_t ez = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
+    if (ez != cudaSuccess) return cuda_err(ctx, ez, "cudaMemsetAsync");
     if (ctx->tune.C > 0) {
         // one persistent launch integrates every step; no wavefield in HBM
         ctx->last_steps_launches = ctx->g.nsteps;
@@ -367,6 +370,22 @@ int oed_autotune(oed_ctx *ctx, int nsolve, void *stream)
     ctx->tune = best;
     drop_graphs(ctx);   // captured loops used the previous shape
     return OED_OK;
+}
+
+int oed_wait_selftest(oed_ctx *ctx, double seconds, void *stream)
+{
+    if (!ctx) return OED_EINVAL;
+    if (!(seconds > 0.0) || seconds > 2.0)
+        return set_err(ctx, OED_EINVAL, "oed_wait_selftest: seconds must be in (0, 2]");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_wait_selftest(ctx, (unsigned long long)(seconds * 1e9), st);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "oed_wait_selftest");
+    return flag ? set_err(ctx, OED_ETIMEOUT, "oed_wait_selftest: the bounded wait expired as intended")
+                : set_err(ctx, OED_ECUDA, "oed_wait_selftest: the wait ended without an arrival");
 }
 
 int oed_get_tuning(const oed_ctx *ctx, int *cluster_size, int *rows_per_thread, int *warps_per_block)

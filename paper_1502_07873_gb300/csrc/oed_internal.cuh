@@ -106,7 +106,8 @@ struct oed_ctx {
     void *d_rows = nullptr;    // RowCoef<real>[nz]
     void *d_fac = nullptr;     // FacCoef<real>[nz] (same rows, factored form)
     int *d_rec = nullptr;      // [nrec]
-    int *d_err = nullptr;      // device flag: a bounded wait in a kernel expired
+    int *d_err = nullptr;      // device flag: a bounded wait in a kernel expired (cleared
+                               // before every time loop, read when the Hessians are combined)
     void *d_u0 = nullptr;      // wavefield level buffer A [max_solves][2][nz][xp]
     void *d_u1 = nullptr;      // wavefield level buffer B
     void *d_src = nullptr;     // SourceDesc<real>[max_solves]
@@ -159,6 +160,7 @@ bool tma_supported(const oed_ctx *ctx);
 int tma_prepare(oed_ctx *ctx);
 cudaError_t launch_steps_tma(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0,
                              cudaEvent_t ev1, int nsteps_override);
+cudaError_t launch_wait_selftest(const oed_ctx *ctx, unsigned long long limit_ns, cudaStream_t st);
 
 // resident.cu
 int resident_cluster_size(const oed_ctx *ctx);

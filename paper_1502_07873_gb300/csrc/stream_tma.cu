@@ -83,8 +83,9 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// wait for the phase with the given parity, bounded by kWaitLimitNs; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+// wait for the phase with the given parity, bounded by limit_ns; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
+                                          unsigned long long limit_ns = kWaitLimitNs)
 {
     const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
     const unsigned long long t0 = global_ns();
@@ -96,8 +97,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
                      : "r"(a), "r"(parity)
                      : "memory");
         if (ok) return true;
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
+}
+
+// Self-test of the bounded wait: one CTA waits for the first phase of a barrier that
+// expects one arrival and never gets it, so the wait can only end by its limit; it
+// then raises the same device flag as the streaming kernel does.
+__global__ void k_wait_selftest(int *err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, limit_ns);
+    __syncthreads();
+    if (threadIdx.x == 0 && !ok) atomicExch(err, 1);
 }
 
 __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, int x, int y, int z,
@@ -319,6 +333,12 @@ static bool make_map(CUtensorMap *map, void *base, const Geometry &g, int nsolve
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_wait_selftest(const oed_ctx *ctx, unsigned long long limit_ns, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(ctx->d_err, limit_ns);
+    return cudaGetLastError();
 }
 
 bool tma_supported(const oed_ctx *ctx)
