@@ -117,3 +117,67 @@ def test_time_function_kind_is_validated_on_the_host(P):
         sizes[jac] = L.oed_server_request_bytes(ctypes.byref(req), 16)
     assert sizes[P.OED_JAC_PAIRS] > sizes[P.OED_JAC_DIFFERENCE] > 0
     assert sizes[P.OED_JAC_SENSITIVITY] == 0
+
+
+_CTYPE_OF = {"int": ctypes.c_int, "double": ctypes.c_double, "size_t": ctypes.c_size_t,
+             "unsigned long long": ctypes.c_ulonglong, "unsigned int": ctypes.c_uint,
+             "unsigned": ctypes.c_uint}
+
+
+def _prototypes():
+    src = open(os.path.join(ROOT, "include", "oed.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    out = {}
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(oed_[a-z_]+)\s*\(([^)]*)\)\s*;", src):
+        params = [p.strip() for p in m.group(3).split(",")]
+        out[m.group(2)] = [] if params == ["void"] or params == [""] else params
+    return out
+
+
+def test_binding_argument_types_match_the_header(P):
+    """Every prototype of include/oed.h and the binding's argtypes agree in arity and in
+    kind: pointers for pointer parameters, int / double / size_t for the scalars."""
+    L = P.library()
+    protos = _prototypes()
+    assert set(protos) == set(P.SYMBOLS)
+    for name, params in protos.items():
+        argtypes = getattr(L, name).argtypes
+        assert len(argtypes) == len(params), (name, params, argtypes)
+        for p, t in zip(params, argtypes):
+            if "*" in p:
+                assert t is ctypes.c_void_p or t is ctypes.c_char_p or hasattr(t, "contents") or \
+                    issubclass(t, ctypes._Pointer), (name, p, t)
+            else:
+                words = p.replace("const", "").split()[:-1]   # the type, without the name
+                assert t is _CTYPE_OF[" ".join(words)], (name, p, t)
+
+
+def test_struct_mirrors_match_the_c_layout(P, tmp_path):
+    """The ctypes mirrors of oed_problem, oed_request and oed_result have the C sizes and
+    field offsets (compiled and measured with the host C compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"oed_problem": P.Problem, "oed_request": P.Request, "oed_result": P.Result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "oed.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line:
+            s, f, v = line.split()
+            got[(s, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
