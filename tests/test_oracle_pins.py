@@ -835,3 +835,46 @@ def test_forward_with_either_time_function_is_the_forward_of_its_forcing(oracle)
         assert np.max(np.abs(g)) > 0
         assert np.array_equal(g, oracle.forward_field(G, f))
     assert not np.allclose(oracle.forward(G, th, stf=oracle.STF_RICKER), oracle.forward(G, th))
+
+
+# ------------------------------------------------------------------ media (Sec. 2.1)
+def test_media_recover_the_wave_speeds_and_the_interface_rule(oracle):
+    """The Lame parameters the oracle builds give back the layer's wave speeds through
+    c_p = sqrt((lambda + 2 mu)/rho) and c_s = sqrt(mu/rho) (Sec. 2.1), and a node lying
+    exactly on an interface takes the deeper layer (the reading both sides use)."""
+    h = 25.0
+    layers = ((0.0, 2000.0, 1155.0, 2200.0), (300.0, 3000.0, 1732.0, 2500.0), (612.5, 4500.0, 2598.0, 2700.0))
+    G = oracle.Grid(9, 40, h, 1e-3, 1, layers, [0])
+    lam, mu, nu = (a.reshape(40, 9) for a in (G.lam, G.mu, G.nu))
+    for j in range(40):
+        z = j * h
+        expect = 0 if z < 300.0 else (1 if z < 612.5 else 2)
+        _, vp, vs, rho = layers[expect]
+        assert np.all(np.abs(np.sqrt((lam[j] + 2 * mu[j]) / nu[j]) - vp) < 1e-9 * vp)
+        assert np.all(np.abs(np.sqrt(mu[j] / nu[j]) - vs) < 1e-9 * vs)
+        assert np.all(nu[j] == rho)
+    assert nu[12, 0] == 2500.0 and nu[11, 0] == 2200.0   # z = 300 m sits on the interface
+    assert nu[24, 0] == 2500.0 and nu[25, 0] == 2700.0   # 612.5 m lies between nodes 24 and 25
+
+
+def test_p_waves_travel_at_the_p_speed(oracle):
+    """An explosive source (m_xx = m_zz, m_xz = 0) radiates P waves only; their onset at
+    two surface receivers 800 m and 1000 m from the source is separated by the P travel
+    time of the 200 m difference, 200 / c_p (grid dispersion is negligible at 30 nodes per
+    wavelength), and the near onset precedes t_s + 800 / c_p by at most the pulse's
+    half-width.  A slip in the Lame parameters or in the operator's (lambda + 2 mu) terms
+    changes the speed by far more than the two-step tolerance."""
+    h, vp, vs, rho = 10.0, 3000.0, 1732.0, 2500.0
+    dt = 0.5 * h / vp
+    nsteps = int(0.5 / dt)
+    G = oracle.Grid(201, 121, h, dt, nsteps, ((0.0, vp, vs, rho),), [100, 160])
+    ts, om = 0.1, 60.0
+    g = oracle.forward(G, [1000.0, 800.0, ts, om, 1e13, 0.0, 1e13])
+    t = np.arange(nsteps + 1) * dt
+    onset = []
+    for r in range(2):
+        u = np.hypot(g[:, r, 0], g[:, r, 1])
+        onset.append(t[np.argmax(u > 0.05 * u.max())])
+    assert abs((onset[1] - onset[0]) - 200.0 / vp) <= 2 * dt
+    assert ts + 800.0 / vp - 4.0 / om <= onset[0] <= ts + 800.0 / vp
+    assert np.max(np.abs(g[:, 0, 0])) == 0.0   # the receiver above the source: u_x = 0 by symmetry
