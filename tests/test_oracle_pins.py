@@ -878,3 +878,20 @@ def test_p_waves_travel_at_the_p_speed(oracle):
     assert abs((onset[1] - onset[0]) - 200.0 / vp) <= 2 * dt
     assert ts + 800.0 / vp - 4.0 / om <= onset[0] <= ts + 800.0 / vp
     assert np.max(np.abs(g[:, 0, 0])) == 0.0   # the receiver above the source: u_x = 0 by symmetry
+
+
+def test_s_waves_travel_at_the_s_speed(oracle):
+    """A shear source (m_xz only) radiates no P wave straight up; the strongest motion at
+    the receiver above it is the S pulse, peaking within a pulse half-width (1/omega_s) of
+    t_s + 800 / c_s.  Checked for two shear speeds, so a slip in mu or in the mu terms of
+    the operator moves the peak by more than the tolerance."""
+    h, vp, rho = 10.0, 3000.0, 2500.0
+    dt = 0.5 * h / vp
+    nsteps = int(0.75 / dt)
+    ts, om = 0.1, 60.0
+    t = np.arange(nsteps + 1) * dt
+    for vs in (1732.0, 1500.0):
+        G = oracle.Grid(201, 121, h, dt, nsteps, ((0.0, vp, vs, rho),), [100])
+        g = oracle.forward(G, [1000.0, 800.0, ts, om, 0.0, 1e13, 0.0])
+        u = np.hypot(g[:, 0, 0], g[:, 0, 1])
+        assert abs(t[np.argmax(u)] - (ts + 800.0 / vs)) < 1.0 / om, vs
