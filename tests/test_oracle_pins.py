@@ -895,3 +895,40 @@ def test_s_waves_travel_at_the_s_speed(oracle):
         g = oracle.forward(G, [1000.0, 800.0, ts, om, 0.0, 1e13, 0.0])
         u = np.hypot(g[:, 0, 0], g[:, 0, 1])
         assert abs(t[np.argmax(u)] - (ts + 800.0 / vs)) < 1.0 / om, vs
+
+
+def _rayleigh_speed(vp, vs):
+    """Root of the Rayleigh equation (2 - x)^2 = 4 sqrt(1 - x) sqrt(1 - x vs^2/vp^2), x = (c/vs)^2."""
+    k = (vs / vp) ** 2
+    f = lambda x: (2 - x) ** 2 - 4 * math.sqrt(1 - x) * math.sqrt(1 - x * k)
+    lo, hi = 0.5, 0.999
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(lo) * f(mid) <= 0:
+            hi = mid
+        else:
+            lo = mid
+    return vs * math.sqrt(0.5 * (lo + hi))
+
+
+def test_free_surface_carries_rayleigh_waves_at_the_rayleigh_speed(oracle):
+    """A shallow explosive source under the free surface of a Poisson solid (lambda = mu)
+    sends a Rayleigh pulse along it; the lag that best aligns u_z at surface receivers 600 m
+    and 1000 m away (cross-correlation, parabolic refinement) gives its speed, which must
+    be the root of the Rayleigh equation, c_R = 0.9194 c_s, within 1% at h = 10 m (0.35%
+    measured, 0.02% at 5 m), and not c_s.  This pins the traction-free closure of the
+    surface row against a textbook closed form."""
+    h, vp, vs, rho = 10.0, 3000.0, 1732.0, 2500.0
+    cR = _rayleigh_speed(vp, vs)
+    assert abs(cR / vs - 0.9194) < 1e-3
+    dt = 0.5 * h / vp
+    nsteps = int(1.0 / dt)
+    G = oracle.Grid(261, 81, h, dt, nsteps, ((0.0, vp, vs, rho),), [110, 150])
+    g = oracle.forward(G, [500.0, 40.0, 0.1, 60.0, 1e13, 0.0, 1e13])
+    a, b = g[:, 0, 1], g[:, 1, 1]
+    c = np.correlate(b, a, mode="full")[len(a) - 1:]
+    k = int(np.argmax(c))
+    lag = (k + 0.5 * (c[k - 1] - c[k + 1]) / (c[k - 1] - 2 * c[k] + c[k + 1])) * dt
+    speed = 400.0 / lag
+    assert abs(speed / cR - 1) < 0.01, (speed, cR)
+    assert abs(speed / vs - 1) > 0.05
