@@ -932,3 +932,40 @@ def test_free_surface_carries_rayleigh_waves_at_the_rayleigh_speed(oracle):
     speed = 400.0 / lag
     assert abs(speed / cR - 1) < 0.01, (speed, cR)
     assert abs(speed / vs - 1) > 0.05
+
+
+def test_layer_interface_reflects_with_the_impedance_contrast(oracle):
+    """A plane P pulse (a line force f_z along a whole row, 200 m deep) meets a welded
+    interface at 600 m; at the surface the particle velocity of the reflected pulse over
+    that of the direct one is the normal-incidence displacement reflection coefficient
+    (Z1 - Z2) / (Z1 + Z2), Z = rho c_p (both pulses are doubled alike by the free surface),
+    to 5% (1.1% measured with 25 nodes per wavelength); the reflection arrives after the
+    1000 m two-way path to within one node spacing (the interface node belongs to the
+    deeper layer)."""
+    h = 20.0
+    l1, l2 = (0.0, 3000.0, 1732.0, 2500.0), (600.0, 4500.0, 2598.0, 2700.0)
+    nx, nz = 201, 61
+    dt = 0.5 * h / l2[1]
+    nsteps = int(0.55 / dt)
+    G = oracle.Grid(nx, nz, h, dt, nsteps, (l1, l2), [100])
+    om, ts = 40.0, 0.12
+    f = np.zeros((nsteps, 2, nz, nx))
+    for m in range(nsteps):
+        f[m, 1, 10, :] = oracle.stf(m * dt, ts, om)
+    uz = oracle.forward_field(G, f)[:, 0, 1]
+    v = np.diff(uz) / dt
+    t = (np.arange(nsteps) + 0.5) * dt
+    w = 3.0 / om
+
+    def pulse(t_expect):
+        sel = (t > t_expect - w) & (t < t_expect + w)
+        k = np.argmax(np.abs(v[sel]))
+        return v[sel][k], t[sel][k]
+
+    vd, td = pulse(ts + 200.0 / l1[1])
+    vr, tr = pulse(ts + 1000.0 / l1[1])
+    Z1, Z2 = l1[3] * l1[1], l2[3] * l2[1]
+    R = (Z1 - Z2) / (Z1 + Z2)
+    assert abs(vr / vd - R) < 0.05 * abs(R), (vr / vd, R)
+    assert abs(td - (ts + 200.0 / l1[1])) < 2 * dt
+    assert abs(tr - (ts + 1000.0 / l1[1])) < h / l1[1] + 2 * dt
