@@ -969,3 +969,28 @@ def test_layer_interface_reflects_with_the_impedance_contrast(oracle):
     assert abs(vr / vd - R) < 0.05 * abs(R), (vr / vd, R)
     assert abs(td - (ts + 200.0 / l1[1])) < 2 * dt
     assert abs(tr - (ts + 1000.0 / l1[1])) < h / l1[1] + 2 * dt
+
+
+def test_absorbing_bottom_passes_a_normally_incident_pulse(oracle):
+    """The first-order absorbing bottom row is exact for normal incidence in the continuum;
+    a plane P pulse (line force along a row) that reaches it returns to the surface with
+    under 5% of the direct pulse's particle velocity (2.2% measured at 25 nodes per
+    wavelength).  Taking c_s for the normal component there would reflect (c_p - c_s) /
+    (c_p + c_s) = 27%."""
+    h = 20.0
+    layer = (0.0, 3000.0, 1732.0, 2500.0)
+    nx, nz = 201, 31   # bottom row at 600 m
+    dt = 0.5 * h / layer[1]
+    nsteps = int(0.6 / dt)
+    G = oracle.Grid(nx, nz, h, dt, nsteps, (layer,), [100])
+    om, ts = 40.0, 0.12
+    f = np.zeros((nsteps, 2, nz, nx))
+    for m in range(nsteps):
+        f[m, 1, 10, :] = oracle.stf(m * dt, ts, om)
+    uz = oracle.forward_field(G, f)[:, 0, 1]
+    v = np.diff(uz) / dt
+    t = (np.arange(nsteps) + 0.5) * dt
+    w = 3.0 / om
+    direct = np.max(np.abs(v[(t > ts + 200 / 3000.0 - w) & (t < ts + 200 / 3000.0 + w)]))
+    back = np.max(np.abs(v[(t > ts + 1000 / 3000.0 - w) & (t < ts + 1000 / 3000.0 + w)]))
+    assert back < 0.05 * direct, back / direct
