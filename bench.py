@@ -147,18 +147,24 @@ def kernel_sources_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per cell-update of a stencil kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel sources changed since."""
+def ncu_entry(kernel: str):
+    """The committed ncu figures of a stencil kernel, or None when the summary is missing
+    or the kernel's code changed since they were taken."""
     p = os.path.join(ROOT, "profiles", "stencil_dram_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f)
-    e = d.get(kernel)
+        e = json.load(f).get(kernel)
     if not e or e.get("sources_sha") != kernel_sources_hash(kernel):
         return None
-    return float(e["dram_bytes_per_cell_update"])
+    return e
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per cell-update of a stencil kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel's code changed since."""
+    e = ncu_entry(kernel)
+    return float(e["dram_bytes_per_cell_update"]) if e else None
 
 
 class ClockSampler:
@@ -419,6 +425,12 @@ def run_ours(args, rank, world, local):
                     "traffic": (tb * cells if tb is not None else None), "launch_ms": launch_ms,
                     "hbm_equivalent": {"gbs": hbm_equiv, "frac_of_measured_hbm": hbm_equiv / peak,
                                        "note": "24 B per cell-update a streaming kernel would move"}}
+        onchip = ncu_entry("k_resident")
+        if onchip and "l1tex_throughput_frac_active" in onchip:
+            # the unit that binds the resident kernel: L1 / shared memory (ncu, committed)
+            roofline["on_chip"] = {"l1tex_throughput_frac_active": onchip["l1tex_throughput_frac_active"],
+                                   "shared_wavefronts_frac_elapsed": onchip["shared_wavefronts_frac_elapsed"],
+                                   "source": "ncu --set full of the same code, 60 solves (profiles/)"}
         launches_per_step = 5
     else:
         kname = "k_step_tma" if tuning[0] < 0 else "k_step"
