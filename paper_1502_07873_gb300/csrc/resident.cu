@@ -7,11 +7,13 @@
 //     A, B : [R][npair + 2] float4,   coef : [R] KP (FacCoef in (x, z) pairs),   the solve's 2 x 49
 //     source weights (kept on chip: read from global memory every step they put an L1
 //     round trip on the critical path of the warps that own the patch columns)
-// Slot q of a row holds the column pair p = q - 1 as (x_2p, z_2p, x_2p+1, z_2p+1);
-// slots 0 and npair + 1 (columns -2, -1, nx.., and column nx when nx is odd) are
-// zero ghosts, so a thread owning pair p reads its whole neighbourhood with one
-// 128-bit load (its pair) and two 64-bit loads (the west column of slot p and the
-// east column of slot p + 2), both components at once.  Level m lives in A (m
+// A row stores the even columns' (x, z) in sq = npair + 2 float2 slots, then the odd
+// columns' in sq more; slot q of each half belongs to the column pair p = q - 1, and
+// slots 0 and npair + 1 (columns -2, -1, nx.., and column nx when nx is odd) are zero
+// ghosts.  A thread owning pair p reads its whole neighbourhood, both components at
+// once, with four 64-bit loads (its two columns, the west column from the odd half
+// and the east column from the even half), each at an 8-byte stride across the
+// warp: no bank conflicts.  Level m lives in A (m
 // even) or B (m odd); u^{m+1} overwrites u^{m-1} in place.  The rows just above
 // and below a CTA's slab are read straight from the neighbouring CTA's shared
 // memory (mapa + ld.shared::cluster).  One cluster barrier (arrive.release /
@@ -82,16 +84,6 @@ __device__ __forceinline__ unsigned remote_addr(unsigned local, unsigned rank)
     unsigned r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
     return r;
-}
-
-__device__ __forceinline__ float4 ld_cluster4(unsigned addr)
-{
-    float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(addr)
-                 : "memory");
-    return v;
 }
 
 __device__ __forceinline__ float2 ld_cluster2(unsigned addr)
@@ -205,25 +197,47 @@ __device__ __forceinline__ void absorbingP(float2 cpcs, float4 nv, const Row2P &
     }
 }
 
-// q points at the thread's own slot of a local row
-__device__ __forceinline__ void load_row(const float4 *q, Row2P &r)
+// A shared row holds the even columns' (x, z) in its first sq float2 slots and the odd
+// columns' in the next sq: slot q of each half belongs to the column pair p = q - 1, so
+// the pair of a thread is (E[q], O[q]), its west column O[q-1] and its east column
+// E[q+1] -- four 64-bit loads at an 8-byte stride across the warp, no bank conflicts.
+// q points at the thread's even slot of the row.
+__device__ __forceinline__ float4 pair_at(const float2 *q, int sq)
 {
-    const float2 w = *reinterpret_cast<const float2 *>(&q[-1].z);
-    const float2 e = *reinterpret_cast<const float2 *>(&q[1].x);
-    row_fromP(w, *q, e, r);
+    const float2 e = q[0], o = q[sq];
+    return make_float4(e.x, e.y, o.x, o.y);
 }
 
-// the same slot of a row in CTA `nb` of the cluster
-__device__ __forceinline__ void load_row_remote(const float4 *q, unsigned nb, Row2P &r)
+__device__ __forceinline__ void pair_put(float2 *q, int sq, float4 u)
+{
+    q[0] = make_float2(u.x, u.y);
+    q[sq] = make_float2(u.z, u.w);
+}
+
+__device__ __forceinline__ void load_row(const float2 *q, int sq, Row2P &r)
+{
+    row_fromP(q[sq - 1], pair_at(q, sq), q[1], r);
+}
+
+// the same slots of a row in CTA `nb` of the cluster
+__device__ __forceinline__ float4 pair_at_remote(const float2 *q, int sq, unsigned nb)
 {
     const unsigned b = remote_addr(smem_addr(q), nb);
-    row_fromP(ld_cluster2(b - 8u), ld_cluster4(b), ld_cluster2(b + 16u), r);
+    const float2 e = ld_cluster2(b), o = ld_cluster2(b + 8u * (unsigned)sq);
+    return make_float4(e.x, e.y, o.x, o.y);
+}
+
+__device__ __forceinline__ void load_row_remote(const float2 *q, int sq, unsigned nb, Row2P &r)
+{
+    const unsigned b = remote_addr(smem_addr(q), nb);
+    const float2 e = ld_cluster2(b), o = ld_cluster2(b + 8u * (unsigned)sq);
+    row_fromP(ld_cluster2(b + 8u * (unsigned)(sq - 1)), make_float4(e.x, e.y, o.x, o.y), ld_cluster2(b + 8u), r);
 }
 
 // float offset of node (column i, component comp) within a shared row
-__device__ __forceinline__ int node_off(int i, int comp)
+__device__ __forceinline__ int node_off(int i, int comp, int sq)
 {
-    return ((i >> 1) + 1) * 4 + (i & 1) * 2 + comp;
+    return 2 * ((i & 1) ? sq + (i >> 1) + 1 : (i >> 1) + 1) + comp;
 }
 
 __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
@@ -235,8 +249,9 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     const int R = a.R, sq = a.sq;
     const int j0 = (int)rank * R;
     const int nrows = max(0, min(R, g.nz - j0));
-    const int lvl = R * sq;   // float4 slots per level
-    float4 *A = smem4, *B = smem4 + lvl;
+    const int lvl = R * sq;   // 16-byte units per level
+    const int RS = 2 * sq;    // float2 slots per row
+    float2 *A = reinterpret_cast<float2 *>(smem4), *B = A + R * RS;
     KP *coef = reinterpret_cast<KP *>(smem4 + 2 * lvl);
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -269,39 +284,39 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     cluster_barrier();
 
     for (int m = 0; m < g.nsteps; m++) {
-        const float4 *cur = ((m & 1) ? B : A) + p + 1;   // this thread's slot in row 0
-        float4 *nxt = ((m & 1) ? A : B) + p + 1;
+        const float2 *cur = ((m & 1) ? B : A) + p + 1;   // this thread's even slot in row 0
+        float2 *nxt = ((m & 1) ? A : B) + p + 1;
         if (rank == 0) {
             const float *row0 = reinterpret_cast<const float *>((m & 1) ? B : A);
             for (int q = tid; q < 2 * g.nrec; q += nthr)
-                trace[(size_t)m * g.nrec * 2 + q] = row0[node_off(a.rec[q >> 1], q & 1)];
+                trace[(size_t)m * g.nrec * 2 + q] = row0[node_off(a.rec[q >> 1], q & 1, sq)];
         }
         if (active && l0 < l1) {
             Row2P rn, rc, rs;
             int l = l0;
-            load_row(cur + l * sq, rc);
+            load_row(cur + l * RS, sq, rc);
             if (top) {   // surface row: no north differences, cross terms on the row itself
                 if (l + 1 < nrows)
-                    load_row(cur + (l + 1) * sq, rs);
+                    load_row(cur + (l + 1) * RS, sq, rs);
                 else   // a one-row slab
-                    load_row_remote(cur, rank + 1, rs);
+                    load_row_remote(cur, sq, rank + 1, rs);
                 southP(rc, rs);
                 Row2P nt = rc;
                 nt.va = nt.vb = make_float2(0.0f, 0.0f);
-                float4 *o = nxt + l * sq;
-                float4 u = *o;
+                float2 *o = nxt + l * RS;
+                float4 u = pair_at(o, sq);
                 const KP K = coef[l];
                 pair_updateP(K, nt, rc, rs, u);
                 if (kind) absorbingP(K.c, u, rc, false, kind, u);
-                *o = u;
+                pair_put(o, sq, u);
                 rn = rc;
                 rc = rs;
                 l++;
             } else {
                 if (l > 0)
-                    load_row(cur + (l - 1) * sq, rn);
+                    load_row(cur + (l - 1) * RS, sq, rn);
                 else
-                    load_row_remote(cur + (R - 1) * sq, rank - 1, rn);
+                    load_row_remote(cur + (R - 1) * RS, sq, rank - 1, rn);
                 southP(rn, rc);
             }
             // rows whose south neighbour is a local row and that are not the bottom row:
@@ -309,12 +324,12 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
             const int lstop = min(l1, nrows - 1);
             if (l < lstop) {
                 // the loads of the next row are issued before the update of this one
-                const float4 *sp = cur + (l + 1) * sq;
-                float4 *o = nxt + l * sq;
+                const float2 *sp = cur + (l + 1) * RS;
+                float2 *o = nxt + l * RS;
                 const KP *cf = coef + l;
-                float4 pm = sp[0], pu = o[0];
-                float2 pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
-                float2 pe = *reinterpret_cast<const float2 *>(&sp[1].x);
+                float4 pm = pair_at(sp, sq), pu = pair_at(o, sq);
+                float2 pw = sp[sq - 1];
+                float2 pe = sp[1];
                 // side: the warp holds a side column (absorbing patch compiled in);
                 // pf: a row below the south row exists, prefetch it (every row but the last)
                 auto march = [&](auto side) {
@@ -322,11 +337,11 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                         row_fromP(pw, pm, pe, ws);
                         float4 u = pu;
                         if constexpr (decltype(pf)::value) {
-                            sp += sq;
-                            pm = sp[0];
-                            pw = *reinterpret_cast<const float2 *>(&sp[-1].z);
-                            pe = *reinterpret_cast<const float2 *>(&sp[1].x);
-                            pu = o[sq];
+                            sp += RS;
+                            pm = pair_at(sp, sq);
+                            pw = sp[sq - 1];
+                            pe = sp[1];
+                            pu = pair_at(o + RS, sq);
                         }
                         southP(wc, ws);
                         const KP K = *cf;
@@ -334,8 +349,8 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                         if constexpr (decltype(side)::value) {
                             if (kind) absorbingP(K.c, u, wc, false, kind, u);
                         }
-                        *o = u;
-                        o += sq;
+                        pair_put(o, sq, u);
+                        o += RS;
                         cf++;
                     };
                     const std::true_type P{};
@@ -376,19 +391,19 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
             // or the absorbing bottom row
             for (; l < l1; l++) {
                 const KP K = coef[l];
-                float4 *o = nxt + l * sq;
-                float4 u = *o;
+                float2 *o = nxt + l * RS;
+                float4 u = pair_at(o, sq);
                 if (j0 + l == g.nz - 1) {
-                    const float4 nv = l > 0 ? cur[(l - 1) * sq]
-                                            : ld_cluster4(remote_addr(smem_addr(cur + (R - 1) * sq), rank - 1));
+                    const float4 nv = l > 0 ? pair_at(cur + (l - 1) * RS, sq)
+                                            : pair_at_remote(cur + (R - 1) * RS, sq, rank - 1);
                     absorbingP(K.c, nv, rc, true, kind, u);
                 } else {
-                    load_row_remote(cur, rank + 1, rs);
+                    load_row_remote(cur, sq, rank + 1, rs);
                     southP(rc, rs);
                     pair_updateP(K, rn, rc, rs, u);
                     if (kind) absorbingP(K.c, u, rc, false, kind, u);
                 }
-                *o = u;
+                pair_put(o, sq, u);
                 rn = rc;
                 rc = rs;
             }
@@ -400,16 +415,16 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 for (int bb = 0; bb < kPatch; bb++) {
                     const int lj = sj + bb - j0;
                     if (lj < l0 || lj >= l1) continue;
-                    float *row = nf + (size_t)lj * sq * 4;
+                    float *row = nf + (size_t)lj * RS * 2;
                     if (scolA) {
-                        row[node_off(c, 0)] = add_force(row[node_off(c, 0)], S, sw[bb * kPatch + siA]);
-                        row[node_off(c, 1)] = add_force(row[node_off(c, 1)], S, sw[kPatch * kPatch + bb * kPatch + siA]);
+                        const int ia = node_off(c, 0, sq);
+                        row[ia] = add_force(row[ia], S, sw[bb * kPatch + siA]);
+                        row[ia + 1] = add_force(row[ia + 1], S, sw[kPatch * kPatch + bb * kPatch + siA]);
                     }
                     if (scolB) {
-                        row[node_off(c + 1, 0)] =
-                            add_force(row[node_off(c + 1, 0)], S, sw[bb * kPatch + siB]);
-                        row[node_off(c + 1, 1)] =
-                            add_force(row[node_off(c + 1, 1)], S, sw[kPatch * kPatch + bb * kPatch + siB]);
+                        const int ib = node_off(c + 1, 0, sq);
+                        row[ib] = add_force(row[ib], S, sw[bb * kPatch + siB]);
+                        row[ib + 1] = add_force(row[ib + 1], S, sw[kPatch * kPatch + bb * kPatch + siB]);
                     }
                 }
             }
@@ -419,7 +434,7 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     if (rank == 0) {
         const float *row0 = reinterpret_cast<const float *>((g.nsteps & 1) ? B : A);
         for (int q = tid; q < 2 * g.nrec; q += nthr)
-            trace[(size_t)g.nsteps * g.nrec * 2 + q] = row0[node_off(a.rec[q >> 1], q & 1)];
+            trace[(size_t)g.nsteps * g.nrec * 2 + q] = row0[node_off(a.rec[q >> 1], q & 1, sq)];
     }
 }
 
