@@ -54,7 +54,7 @@ struct ResArgs {
     const int *rec;                // [nrec]
     Geometry g;
     int R;                         // rows per CTA
-    int sq;                        // float4 slots per shared row, npair + 2
+    int sq;                        // float2 slots per half row (npair + 2); a row is 2 sq
     int npair;                     // column pairs per row, (nx + 1) / 2
     int nseg;                      // row segments per column pair
     int rps;                       // rows per segment
