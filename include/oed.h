@@ -45,7 +45,7 @@ extern "C" {
 #define OED_ECUDA 4    /* a CUDA runtime call failed */
 #define OED_ETIMEOUT 5 /* a bounded wait gave up */
 #define OED_PENDING 6  /* (serving) the request has not finished yet */
-#define OED_ECANCELED 7 /* (serving) the request was cancelled before it ran */
+#define OED_ECANCELED 7 /* (serving) the request was cancelled (before it ran, or between chunks) */
 
 #define OED_FP32 0 /* stencil time stepping in FP32 (Jacobian, H_1, log-det in FP64) */
 #define OED_FP64 1 /* everything in FP64 */
@@ -105,6 +105,20 @@ size_t oed_workspace_bytes(const oed_problem *p, int max_solves);
  * stream), so creating and destroying contexts does not stall other streams. */
 int oed_destroy(oed_ctx *ctx);
 
+/* Re-target a context at another problem with the same nx, nz and precision,
+ * reusing its device workspace (no allocation): the time-step count, medium,
+ * receivers and time function may differ, as long as the new problem's workspace
+ * for the context's max_solves (oed_workspace_bytes) fits in the context's.  This
+ * is how a server keeps one workspace per grid shape resident across requests.
+ * Captured time loops are dropped; the kernel choice (oed_autotune /
+ * oed_set_tuning), which depends only on the grid shape, is kept.  Streams that
+ * ran earlier calls on the context must be synchronised first.  Returns OED_OK,
+ * OED_EINVAL (malformed problem, another shape or precision, or sensitivity
+ * solves with a non-Gaussian time function), OED_ENOMEM (the workspace does not
+ * fit; the context is unchanged) or OED_ECUDA.  Not in the paper: a systems
+ * call of the serving layer. */
+int oed_rebind(oed_ctx *ctx, const oed_problem *p);
+
 /* Message of the last failing call on ctx (never NULL). */
 const char *oed_last_error(const oed_ctx *ctx);
 
@@ -119,13 +133,15 @@ const char *oed_status_string(int status);
  *   launches  host [1] or NULL: stencil launches in that interval (0 if none yet) */
 int oed_last_step_time(const oed_ctx *ctx, float *ms, int *launches);
 
-/* Time stepping runs in one of two kernels:
+/* Time stepping runs in one of three kernels:
  *  - streaming: one launch per step over all solves, wavefields in HBM
  *    (any grid, FP32 or FP64), replayed from a captured CUDA graph;
+ *  - TMA streaming (FP32): the same, with halo tiles moved by the tensor-memory
+ *    accelerator into a persistent CTA's mbarrier ring (cluster_size -1);
  *  - cluster-resident (FP32, grids whose two time levels fit in the shared
  *    memory of a cluster of C <= 8 CTAs, e.g. 401x201): one launch for all
  *    steps, one thread-block cluster per solve, wavefield kept on chip.
- * Both give the same node updates.  oed_autotune times every streaming launch
+ * All give the same node updates, bit for bit.  oed_autotune times every streaming launch
  * shape (rows marched per thread 2/4/8 x warps per block 1/2/4/8) and every
  * feasible cluster size on nsolve solves of this context's grid, keeps the
  * fastest for later calls, and synchronises the stream.  It overwrites the
@@ -340,15 +356,42 @@ int oed_eig_host(oed_ctx *ctx, const double *theta, const double *w, int n, cons
  *
  * Requests (a problem, its quadrature nodes and weights, the prior box, the FD
  * step, the noise level and the Jacobian form) are queued in arrival order.  Up
- * to max_active requests run at once, each on its own worker thread and CUDA
- * stream through oed_create / oed_hessian / oed_eig, so a request admitted while
- * others are on the GPU overlaps with them on the device.  The head of the queue
- * is admitted as soon as its device footprint (oed_server_request_bytes: context
- * workspace for chunks of chunk_nodes nodes, plus its node, weight and Hessian
- * arrays) fits in the part of hbm_budget_bytes not held by running requests;
- * admission is strictly first-come first-served.  Launch shapes are autotuned on
- * the first request of each grid shape and reused (unless
- * OED_SERVER_NO_AUTOTUNE).  The server uses the CUDA device current at creation.
+ * to max_active requests run at once, each on a worker thread with its own CUDA
+ * stream through the public calls (oed_rebind or oed_create, oed_hessian,
+ * oed_eig), so a request admitted while others are on the GPU overlaps with them
+ * on the device.  A request's device footprint (oed_server_request_bytes) is a
+ * context workspace for chunks of chunk_nodes of its nodes plus its node, weight
+ * and Hessian arrays; a request whose footprint exceeds the whole budget is run in
+ * smaller chunks (halved down to one node) and refused only if even one node does
+ * not fit.
+ *
+ * Workspaces stay resident: a finished request's context goes to an idle pool and
+ * the next request with the same grid shape and precision whose workspace fits
+ * re-targets it (oed_rebind) instead of allocating.  Idle workspaces count against
+ * hbm_budget_bytes and are released, oldest first, when a request of another shape
+ * needs the room.
+ *
+ * Admission takes the oldest queued request that fits in the free budget.  A
+ * younger request may be admitted ahead of the queue's head (which may be waiting
+ * for memory) only while the head has waited less than max_wait_s seconds
+ * (oed_server_set_admission, default 10 s); after that nothing passes it, so no
+ * request starves.
+ *
+ * A request runs chunk by chunk; after each chunk its per-node Hessians are copied
+ * to the host.  oed_server_cancel stops a running request after its current chunk
+ * (a queued one never runs); oed_server_checkpoint returns the nodes finished so
+ * far, and a new request with n_done / H_done set from them resumes the work,
+ * recomputing only the remaining nodes, with the same EIG.
+ *
+ * Every finished request has a one-line JSON record (oed_server_metrics; appended
+ * to a file with oed_server_set_log): id, tag, status, grid, steps, layers,
+ * receivers, nodes, precision, Jacobian form, EIG, queue / run / total seconds,
+ * cell-updates and Gcell-updates/s, footprint, and whether its workspace was
+ * reused.  Launch shapes are autotuned on the first request of each grid shape,
+ * precision and Jacobian form (on that request's chunk of solves) and reused
+ * (unless OED_SERVER_NO_AUTOTUNE).  The server
+ * uses the CUDA device current at creation.  None of this is in the paper: it is
+ * the serving layer around the paper's computation.
  * ------------------------------------------------------------------------ */
 typedef struct oed_server oed_server;
 
@@ -363,6 +406,10 @@ typedef struct {
     double rel_step;       /* FD step as a fraction of the prior width */
     double sigma;          /* noise standard deviation (C_eps = sigma^2 I) */
     int jacobian;          /* OED_JAC_PAIRS, OED_JAC_DIFFERENCE or OED_JAC_SENSITIVITY */
+    int n_done;            /* resume: the first n_done nodes are already done (0..n) */
+    const double *H_done;  /* host [n_done][7][7] their Hessians (oed_server_checkpoint
+                              of a request on the same nodes); NULL when n_done == 0 */
+    unsigned long long tag;/* caller's label, echoed in the metrics line (e.g. a seed) */
 } oed_request;
 
 typedef struct {
@@ -371,22 +418,48 @@ typedef struct {
     int n_bad;             /* nodes rejected as not positive definite */
     double t_submit, t_admit, t_done; /* seconds on the server's monotonic clock */
     size_t footprint_bytes;           /* device memory reserved while it ran */
+    int nodes_done;        /* nodes whose Hessians are finished (resumed ones included) */
+    int workspace_reused;  /* 1 if it ran in a pooled workspace, 0 if it allocated one */
 } oed_result;
 
 int oed_server_create(oed_server **srv, size_t hbm_budget_bytes, int max_active, int chunk_nodes,
                       int flags);
-/* Device bytes a request reserves while it runs (0 if the request is invalid). */
+/* Admission policy: requests may pass the queue's head only while it has waited
+ * less than max_wait_s seconds (>= 0; 0 = strictly first come, first served). */
+int oed_server_set_admission(oed_server *srv, double max_wait_s);
+/* Append each finished request's JSON metrics line to the file at path ("-" =
+ * stderr, NULL = stop logging).  OED_EINVAL if the file cannot be opened. */
+int oed_server_set_log(oed_server *srv, const char *path);
+/* Device bytes a request reserves while it runs at chunks of chunk_nodes nodes
+ * (0 if the request is invalid). */
 size_t oed_server_request_bytes(const oed_request *req, int chunk_nodes);
-/* Queue a request (all of its host data is copied).  OED_ENOMEM if its footprint
- * exceeds the whole budget (it could never be admitted), OED_EINVAL if malformed. */
+/* Queue a request (all of its host data is copied).  OED_ENOMEM if even one node
+ * at a time exceeds the whole budget (it could never be admitted), OED_EINVAL if
+ * malformed. */
 int oed_server_submit(oed_server *srv, const oed_request *req, unsigned long long *id);
 /* Current result of request id (status OED_PENDING until it finishes). */
 int oed_server_poll(oed_server *srv, unsigned long long id, oed_result *out);
 /* Wait up to timeout_s seconds for request id; OED_ETIMEOUT if it is still pending. */
 int oed_server_wait(oed_server *srv, unsigned long long id, double timeout_s, oed_result *out);
-/* Device bytes held by running requests, running and queued request counts. */
+/* Cancel request id: a queued request finishes at once with OED_ECANCELED; a running
+ * one stops after its current chunk with OED_ECANCELED (its finished nodes stay
+ * available to oed_server_checkpoint); a finished one is left as it is.  OED_EINVAL
+ * for an unknown id. */
+int oed_server_cancel(oed_server *srv, unsigned long long id);
+/* The per-node Hessians of request id finished so far, in node order: *nodes_done
+ * is set to their count k; if H is not NULL it receives them, host [k][7][7]
+ * (OED_ENOMEM if cap < k).  Valid while the request runs and after it ends. */
+int oed_server_checkpoint(oed_server *srv, unsigned long long id, double *H, int cap, int *nodes_done);
+/* The JSON metrics line of finished request id, NUL-terminated, into buf[cap];
+ * OED_PENDING if it has not finished, OED_ENOMEM if cap is too small. */
+int oed_server_metrics(oed_server *srv, unsigned long long id, char *buf, size_t cap);
+/* Device bytes reserved (running requests and idle workspaces), running and queued
+ * request counts. */
 int oed_server_stats(oed_server *srv, size_t *in_use, int *active, int *queued);
-/* Cancel queued requests, wait for running ones, stop the workers, free the server. */
+/* Idle pooled workspaces: their count and bytes. */
+int oed_server_pool(oed_server *srv, int *idle, size_t *idle_bytes);
+/* Cancel queued requests, wait for running ones, stop the workers, release the
+ * pooled workspaces, free the server. */
 int oed_server_destroy(oed_server *srv);
 
 /* Allocation-free Gauss-Newton Hessian from seismograms the caller already has.

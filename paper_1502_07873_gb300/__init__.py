@@ -33,7 +33,9 @@ SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_gauss_newton_noalloc", "oed_server_create", "oed_server_request_bytes",
            "oed_server_submit", "oed_server_poll", "oed_server_wait", "oed_server_stats",
            "oed_server_destroy", "oed_eig_subset", "oed_dlmc", "oed_hessian_ii", "oed_newton_step",
-           "oed_hessian_map", "oed_wait_selftest")
+           "oed_hessian_map", "oed_wait_selftest", "oed_rebind", "oed_server_set_admission",
+           "oed_server_set_log", "oed_server_cancel", "oed_server_checkpoint", "oed_server_metrics",
+           "oed_server_pool")
 
 
 class OedError(RuntimeError):
@@ -55,13 +57,15 @@ class Request(ctypes.Structure):
     _fields_ = [("problem", Problem), ("n", ctypes.c_int), ("theta", ctypes.POINTER(ctypes.c_double)),
                 ("w", ctypes.POINTER(ctypes.c_double)), ("lo", ctypes.POINTER(ctypes.c_double)),
                 ("hi", ctypes.POINTER(ctypes.c_double)), ("rel_step", ctypes.c_double),
-                ("sigma", ctypes.c_double), ("jacobian", ctypes.c_int)]
+                ("sigma", ctypes.c_double), ("jacobian", ctypes.c_int), ("n_done", ctypes.c_int),
+                ("H_done", ctypes.POINTER(ctypes.c_double)), ("tag", ctypes.c_ulonglong)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("eig", ctypes.c_double), ("n_bad", ctypes.c_int),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t)]
+                ("t_done", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t),
+                ("nodes_done", ctypes.c_int), ("workspace_reused", ctypes.c_int)]
 
 
 _lib = None
@@ -113,6 +117,13 @@ def library():
         "oed_server_wait": (i, [vp, ctypes.c_ulonglong, d, ctypes.POINTER(Result)]),
         "oed_server_stats": (i, [vp, ctypes.POINTER(sz), ip, ip]),
         "oed_server_destroy": (i, [vp]),
+        "oed_rebind": (i, [vp, ctypes.POINTER(Problem)]),
+        "oed_server_set_admission": (i, [vp, d]),
+        "oed_server_set_log": (i, [vp, ctypes.c_char_p]),
+        "oed_server_cancel": (i, [vp, ctypes.c_ulonglong]),
+        "oed_server_checkpoint": (i, [vp, ctypes.c_ulonglong, dp, i, ip]),
+        "oed_server_metrics": (i, [vp, ctypes.c_ulonglong, ctypes.c_char_p, sz]),
+        "oed_server_pool": (i, [vp, ip, ctypes.POINTER(sz)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -124,7 +135,7 @@ def library():
 
 def _status_name(code: int) -> str:
     names = {0: "OED_OK", 1: "OED_EINVAL", 2: "OED_ENOMEM", 3: "OED_ENOTPD", 4: "OED_ECUDA",
-             5: "OED_ETIMEOUT"}
+             5: "OED_ETIMEOUT", 6: "OED_PENDING", 7: "OED_ECANCELED"}
     return names.get(code, f"status {code}")
 
 
@@ -215,6 +226,14 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def rebind(self, problem: Problem):
+        """Re-target this context's workspace at another problem of the same grid shape and
+        precision (oed_rebind)."""
+        _check(self.handle, library().oed_rebind(self.handle, ctypes.byref(problem)), "oed_rebind")
+        self.problem = problem
+        self.nrec = problem.nrec
+        self.nlev = problem.nsteps + 1
 
     def last_step_time(self):
         """(milliseconds, launches) of the stencil launches of the last time loop."""
@@ -423,16 +442,27 @@ def oed_gauss_newton_noalloc(g, lo, hi, rel_step: float, sigma: float, H, stream
     """Allocation-free H_1[n][7][7] from seismograms g[n][15 or 7][nlev][nrec][2] (FP64,
     device).  For callers that cannot allocate device memory while they run; its scratch
     is a fixed 4 MiB array inside the library, shared by all calls on a device (calls that
-    overlap on the GPU race).  Returns the status code (0 = OED_OK)."""
+    overlap on the GPU race).  Returns the status code (0 = OED_OK).  Shapes and dtypes
+    are checked here: a wrong-sized or FP32 tensor would otherwise be read or written
+    past its end on the device."""
+    import torch
+    if g.dim() != 5 or g.shape[4] != 2 or g.dtype != torch.float64:
+        raise ValueError("g must be a float64 tensor of shape [n][15 or 7][nlev][nrec][2]")
     n, per_node, nlev, nrec = g.shape[0], g.shape[1], g.shape[2], g.shape[3]
+    if H.dtype != torch.float64 or tuple(H.shape) != (n, 7, 7):
+        raise ValueError("H must be a float64 tensor of shape [n][7][7]")
+    if g.device != H.device or g.device.index != torch.cuda.current_device():
+        raise ValueError("g and H must be on the current CUDA device")
     return int(library().oed_gauss_newton_noalloc(_ptr(g), n, per_node, nlev, nrec, _darr(lo),
                                                   _darr(hi), float(rel_step), float(sigma), _ptr(H),
                                                   _stream(stream)))
 
 
 def make_request(problem: Problem, theta, w, lo, hi, rel_step: float, sigma: float,
-                 jacobian: int = OED_JAC_PAIRS) -> Request:
-    """Build an oed_request from host arrays (kept alive on the returned object)."""
+                 jacobian: int = OED_JAC_PAIRS, H_done=None, tag: int = 0) -> Request:
+    """Build an oed_request from host arrays (kept alive on the returned object).  H_done
+    ([k][7][7], from Server.checkpoint of a request on the same nodes) resumes it: the
+    first k nodes are not recomputed."""
     import numpy as np
     r = Request()
     r.problem = problem
@@ -445,6 +475,14 @@ def make_request(problem: Problem, theta, w, lo, hi, rel_step: float, sigma: flo
     r.w = wt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     r.lo, r.hi = r._lo, r._hi
     r.rel_step, r.sigma, r.jacobian = float(rel_step), float(sigma), int(jacobian)
+    if H_done is not None and len(H_done):
+        hd = np.ascontiguousarray(H_done, dtype=np.float64).reshape(-1, 7, 7)
+        if hd.shape[0] > r.n:
+            raise ValueError("H_done has more nodes than the request")
+        r._hd = hd
+        r.n_done = hd.shape[0]
+        r.H_done = hd.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    r.tag = int(tag)
     return r
 
 
@@ -487,6 +525,42 @@ class Server:
         b, a, q = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
         library().oed_server_stats(self.handle, ctypes.byref(b), ctypes.byref(a), ctypes.byref(q))
         return int(b.value), int(a.value), int(q.value)
+
+    def pool(self):
+        """(idle pooled workspaces, their bytes)."""
+        k, b = ctypes.c_int(), ctypes.c_size_t()
+        library().oed_server_pool(self.handle, ctypes.byref(k), ctypes.byref(b))
+        return int(k.value), int(b.value)
+
+    def set_admission(self, max_wait_s: float):
+        _check(None, library().oed_server_set_admission(self.handle, float(max_wait_s)),
+               "oed_server_set_admission")
+
+    def set_log(self, path: Optional[str]):
+        _check(None, library().oed_server_set_log(self.handle, None if path is None else path.encode()),
+               "oed_server_set_log")
+
+    def cancel(self, rid: int):
+        _check(None, library().oed_server_cancel(self.handle, rid), "oed_server_cancel")
+
+    def checkpoint(self, rid: int):
+        """Per-node Hessians finished so far, numpy [k][7][7]."""
+        import numpy as np
+        k = ctypes.c_int()
+        _check(None, library().oed_server_checkpoint(self.handle, rid, None, 0, ctypes.byref(k)),
+               "oed_server_checkpoint")
+        H = np.zeros((max(1, k.value), 7, 7))
+        _check(None, library().oed_server_checkpoint(self.handle, rid,
+                                                     H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                     H.shape[0], ctypes.byref(k)), "oed_server_checkpoint")
+        return H[:k.value]
+
+    def metrics(self, rid: int) -> dict:
+        """The finished request's JSON metrics line, parsed."""
+        import json
+        buf = ctypes.create_string_buffer(4096)
+        _check(None, library().oed_server_metrics(self.handle, rid, buf, 4096), "oed_server_metrics")
+        return json.loads(buf.value.decode())
 
     def close(self):
         if self.handle:

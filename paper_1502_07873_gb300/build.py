@@ -15,9 +15,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liboed.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "source.cu", "stencil.cu", "stream_tma.cu", "resident.cu", "hessian.cu", "logdet.cu", "dlmc.cu", "adjoint.cu",
+SOURCES = ["api.cu", "source.cu", "stencil.cu", "stream_tma.cu", "stream_tma2.cu", "resident.cu", "hessian.cu", "logdet.cu", "dlmc.cu", "adjoint.cu",
            "noalloc.cu", "smolyak.cpp", "server.cpp"]
 HEADERS = [os.path.join(CSRC, "oed_internal.cuh"), os.path.join(CSRC, "stencil_cell.cuh"),
+           os.path.join(CSRC, "nvtx_range.h"), os.path.join(CSRC, "pair_math.cuh"),
+           os.path.join(CSRC, "tma_sync.cuh"),
            os.path.join(ROOT, "include", "oed.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

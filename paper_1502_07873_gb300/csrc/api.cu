@@ -7,6 +7,7 @@
 #include <map>
 #include <new>
 
+#include "nvtx_range.h"
 #include "oed_internal.cuh"
 
 namespace oed {
@@ -75,7 +76,7 @@ static Geometry make_geometry(const oed_problem *p)
 }
 
 struct Sizes {
-    size_t u, src, stf, trace, theta, rows, rec, hseg, err, total;
+    size_t u, u2, src, stf, trace, theta, rows, rec, hseg, err, total;
 };
 
 static Sizes sizes(const Geometry &g, int precision, int max_solves)
@@ -85,6 +86,9 @@ static Sizes sizes(const Geometry &g, int precision, int max_solves)
     Sizes s;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     s.u = al((size_t)max_solves * g.solve_stride * e);
+    // FP32 grids that do not fit on chip keep a second pair of levels for the two-step
+    // kernel (it reads one pair and writes the other)
+    s.u2 = (precision == OED_FP32 && !resident_fits(g)) ? 2 * s.u : 0;
     s.src = al((size_t)max_solves * (precision == OED_FP64 ? sizeof(SourceDesc<double>)
                                                            : sizeof(SourceDesc<float>)));
     s.stf = al((size_t)max_solves * g.nsteps * e);
@@ -95,7 +99,7 @@ static Sizes sizes(const Geometry &g, int precision, int max_solves)
     s.rec = al((size_t)g.nrec * sizeof(int));
     s.hseg = al((size_t)chunk * 16 * g.nrec * 28 * sizeof(double));
     s.err = 256;
-    s.total = 2 * s.u + s.src + s.stf + s.trace + s.theta + s.rows + s.rec + s.hseg + s.err;
+    s.total = 2 * s.u + s.u2 + s.src + s.stf + s.trace + s.theta + s.rows + s.rec + s.hseg + s.err;
     return s;
 }
 
@@ -129,10 +133,14 @@ static int run_steps(oed_ctx *ctx, int nsolve, cudaStream_t st)
             cudaStreamDestroy(cap);
             return cuda_err(ctx, e, "cudaStreamBeginCapture");
         }
-        launch_forward_steps(ctx, nsolve, cap, ctx->ev_steps[0], ctx->ev_steps[1]);
+        const cudaError_t el = launch_forward_steps(ctx, nsolve, cap, ctx->ev_steps[0], ctx->ev_steps[1]);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
+        if (el != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_err(ctx, el, "time loop launch");
+        }
         if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamEndCapture");
         cudaGraphExec_t ex = nullptr;
         e = cudaGraphInstantiate(&ex, graph, 0);
@@ -142,6 +150,43 @@ static int run_steps(oed_ctx *ctx, int nsolve, cudaStream_t st)
     }
     ctx->last_steps_launches = ctx->g.nsteps;
     return cuda_err(ctx, cudaGraphLaunch(it->second, st), "cudaGraphLaunch");
+}
+
+// Lay the workspace arrays out in the single allocation starting at base.
+static void carve(oed_ctx *ctx, char *base, const Sizes &s)
+{
+    char *q = base;
+    ctx->d_u0 = q; q += s.u;
+    ctx->d_u1 = q; q += s.u;
+    ctx->d_u2 = s.u2 ? q : nullptr;
+    ctx->d_u3 = s.u2 ? q + s.u : nullptr;
+    q += s.u2;
+    ctx->d_src = q; q += s.src;
+    ctx->d_stf = q; q += s.stf;
+    ctx->d_trace = q; q += s.trace;
+    ctx->d_theta = (double *)q; q += s.theta;
+    ctx->d_rows = q;
+    ctx->d_fac = q + ((size_t)ctx->g.nz * (ctx->precision == OED_FP64 ? sizeof(RowCoef<double>)
+                                                                       : sizeof(RowCoef<float>)) +
+                      255) / 256 * 256;
+    q += s.rows;
+    ctx->d_rec = (int *)q; q += s.rec;
+    ctx->d_hseg = (double *)q; q += s.hseg;
+    ctx->d_err = (int *)q; q += s.err;
+}
+
+// Problem-dependent contents of the workspace: error flag, defined source descriptors,
+// receiver indices and the rows' stencil coefficients (on the context's own stream).
+static void fill_problem(oed_ctx *ctx)
+{
+    cudaMemsetAsync(ctx->d_err, 0, 256, ctx->own_stream);
+    cudaMemsetAsync(ctx->d_src, 0, (size_t)ctx->max_solves * (ctx->precision == OED_FP64
+                                                                  ? sizeof(SourceDesc<double>)
+                                                                  : sizeof(SourceDesc<float>)),
+                    ctx->own_stream);   // defined descriptors before first use
+    cudaMemcpyAsync(ctx->d_rec, ctx->rec_ix.data(), sizeof(int) * ctx->rec_ix.size(), cudaMemcpyHostToDevice,
+                    ctx->own_stream);
+    launch_rows(ctx, ctx->own_stream);   // synchronises the stream
 }
 
 }  // namespace oed
@@ -159,6 +204,8 @@ const char *oed_status_string(int status)
     case OED_ENOTPD: return "OED_ENOTPD";
     case OED_ECUDA: return "OED_ECUDA";
     case OED_ETIMEOUT: return "OED_ETIMEOUT";
+    case OED_PENDING: return "OED_PENDING";
+    case OED_ECANCELED: return "OED_ECANCELED";
     default: return "unknown";
     }
 }
@@ -217,29 +264,11 @@ int oed_create(oed_ctx **out, const oed_problem *p, int max_solves)
         return e == cudaErrorMemoryAllocation ? OED_ENOMEM : OED_ECUDA;
     }
     ctx->bytes = s.total;
-    char *q = base;
-    ctx->d_u0 = q; q += s.u;
-    ctx->d_u1 = q; q += s.u;
-    ctx->d_src = q; q += s.src;
-    ctx->d_stf = q; q += s.stf;
-    ctx->d_trace = q; q += s.trace;
-    ctx->d_theta = (double *)q; q += s.theta;
-    ctx->d_rows = q;
-    ctx->d_fac = q + ((size_t)ctx->g.nz * (ctx->precision == OED_FP64 ? sizeof(RowCoef<double>)
-                                                                       : sizeof(RowCoef<float>)) +
-                      255) / 256 * 256;
-    q += s.rows;
-    ctx->d_rec = (int *)q; q += s.rec;
-    ctx->d_hseg = (double *)q; q += s.hseg;
-    ctx->d_err = (int *)q; q += s.err;
-    cudaMemsetAsync(ctx->d_err, 0, s.err, ctx->own_stream);
-    cudaMemsetAsync(ctx->d_src, 0, s.src, ctx->own_stream);   // defined descriptors before first use
-    cudaMemcpyAsync(ctx->d_rec, ctx->rec_ix.data(), sizeof(int) * p->nrec, cudaMemcpyHostToDevice,
-                    ctx->own_stream);
+    carve(ctx, base, s);
     cudaEventCreate(&ctx->ev_steps[0]);
     cudaEventCreate(&ctx->ev_steps[1]);
     hessian_init(ctx->own_stream);
-    launch_rows(ctx, ctx->own_stream);
+    fill_problem(ctx);
     e = cudaStreamSynchronize(ctx->own_stream);
     if (e != cudaSuccess) {
         int rc = cuda_err(ctx, e, "oed_create");
@@ -270,6 +299,35 @@ int oed_destroy(oed_ctx *ctx)
     cudaFree(ctx->d_adj);
     delete ctx;
     return OED_OK;
+}
+
+int oed_rebind(oed_ctx *ctx, const oed_problem *p)
+{
+    if (!ctx) return OED_EINVAL;
+    std::string why;
+    if (!problem_ok(p, &why)) return set_err(ctx, OED_EINVAL, "oed_rebind: " + why);
+    if (p->nx != ctx->g.nx || p->nz != ctx->g.nz || p->precision != ctx->precision)
+        return set_err(ctx, OED_EINVAL, "oed_rebind: the grid shape and precision must be the context's");
+    const Geometry g = make_geometry(p);
+    const Sizes s = sizes(g, p->precision, ctx->max_solves);
+    if (s.total > ctx->bytes)
+        return set_err(ctx, OED_ENOMEM, "oed_rebind: the problem's workspace exceeds the context's");
+    if (p->stf != OED_STF_GAUSS && ctx->jac_mode == OED_JAC_SENSITIVITY)
+        return set_err(ctx, OED_EINVAL, "oed_rebind: sensitivity solves need the Gaussian time function");
+    // the caller has synchronised the streams of its earlier calls on this context
+    cudaError_t e = cudaStreamSynchronize(ctx->own_stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "oed_rebind");
+    drop_graphs(ctx);   // captured time loops hold the old problem's sizes
+    ctx->g = g;
+    ctx->stf = p->stf;
+    ctx->z_top.assign(p->z_top, p->z_top + p->nlayers);
+    ctx->vp.assign(p->vp, p->vp + p->nlayers);
+    ctx->vs.assign(p->vs, p->vs + p->nlayers);
+    ctx->rho.assign(p->rho, p->rho + p->nlayers);
+    ctx->rec_ix.assign(p->rec_ix, p->rec_ix + p->nrec);
+    carve(ctx, (char *)ctx->d_u0, s);
+    fill_problem(ctx);
+    return cuda_err(ctx, cudaStreamSynchronize(ctx->own_stream), "oed_rebind");
 }
 
 const char *oed_last_error(const oed_ctx *ctx)
@@ -346,6 +404,24 @@ int oed_autotune(oed_ctx *ctx, int nsolve, void *stream)
             best = ctx->tune;
         }
     }
+    // two-step TMA streaming kernel (FP32 grids that do not fit on chip)
+    if (ctx->d_u2 && tma_supported(ctx) && tma_prepare(ctx) > 0 && tma2_prepare(ctx) > 0) {
+        ctx->tune = StepTuning{best.zs, best.wz, -2};
+        int probe = nrep < ctx->g.nsteps ? nrep : ctx->g.nsteps;
+        probe = probe < 4 ? probe : probe / 2 * 2;
+        const float *last = nullptr;
+        cudaError_t e = launch_steps_tma2(ctx, nsolve, st, e0, e1, 2, &last);   // warm
+        if (e == cudaSuccess) e = launch_steps_tma2(ctx, nsolve, st, e0, e1, probe, &last);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) return fail(e);
+        ms /= probe;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = ctx->tune;
+        }
+    }
     // cluster-resident kernel (FP32 grids whose two levels fit in 1..8 CTAs)
     const int cmin = resident_cluster_size(ctx);
     if (cmin > 0) {
@@ -406,6 +482,10 @@ int oed_set_tuning(oed_ctx *ctx, int cluster_size, int rows_per_thread, int warp
     if (cluster_size == -1) {
         if (!tma_supported(ctx) || tma_prepare(ctx) < 1)
             return set_err(ctx, OED_EINVAL, "oed_set_tuning: the TMA kernel needs FP32");
+    } else if (cluster_size == -2) {
+        if (!ctx->d_u2 || !tma_supported(ctx) || tma_prepare(ctx) < 1 || tma2_prepare(ctx) < 1)
+            return set_err(ctx, OED_EINVAL,
+                           "oed_set_tuning: the two-step TMA kernel needs FP32 and a grid that does not fit on chip");
     } else if (cluster_size != 0) {
         const int cmin = resident_cluster_size(ctx);
         if (cmin == 0 || cluster_size < cmin || cluster_size > 8 ||
@@ -449,6 +529,7 @@ int oed_forward(oed_ctx *ctx, const double *theta, int n, double *g, void *strea
     if (n < 0 || (n > 0 && (!theta || !g))) return set_err(ctx, OED_EINVAL, "oed_forward: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t per = (size_t)ctx->g.nlev * ctx->g.nrec * 2;
+    NvtxRange r("oed_forward");
     for (int off = 0; off < n; off += ctx->max_solves) {
         const int nb = std::min(ctx->max_solves, n - off);
         launch_sources(ctx, theta + (size_t)off * kNT, nb, 1, nullptr, st);
@@ -494,12 +575,20 @@ int oed_hessian(oed_ctx *ctx, const double *theta, int n, const double *lo, cons
     if (seg_end.empty() || seg_end.back() != ctx->g.nlev) seg_end.push_back(ctx->g.nlev);
     cudaStream_t st = (cudaStream_t)stream;
     const int chunk = oed_chunk_nodes(ctx);
+    NvtxRange all("oed_hessian");
     for (int off = 0; off < n; off += chunk) {
         const int nb = std::min(chunk, n - off);
         const int P = solves_per_node(ctx);
-        launch_sources(ctx, theta + (size_t)off * kNT, nb, P, d, st);
-        int rc = run_steps(ctx, nb * P, st);
-        if (rc) return rc;
+        {
+            NvtxRange r("oed_hessian: sources and perturbations");
+            launch_sources(ctx, theta + (size_t)off * kNT, nb, P, d, st);
+        }
+        {
+            NvtxRange r("oed_hessian: stencil time steps");
+            int rc = run_steps(ctx, nb * P, st);
+            if (rc) return rc;
+        }
+        NvtxRange r("oed_hessian: FD Jacobian and J^T J reduction");
         launch_hessian(ctx, nb, inv2d, sigma, seg_end.data(), (int)seg_end.size(), win_seg.data(),
                        nwin, H + (size_t)off * 49,
                        H_rec ? H_rec + (size_t)off * ctx->g.nrec * nwin * 28 : nullptr,
@@ -611,6 +700,7 @@ int oed_eig_subset(oed_ctx *ctx, const double *H, int n, const double *w, const 
         if (!(hi[j] > lo[j])) return set_err(ctx, OED_EINVAL, "oed_eig: need hi > lo");
         logvol += log(hi[j] - lo[j]);
     }
+    NvtxRange r("oed_eig: scaled Cholesky log-det, D_KL-hat, weighted sum");
     launch_eig(H, n, w, logvol, param_mask, eig, dkl, status, n_bad, (cudaStream_t)stream);
     return cuda_err(ctx, cudaGetLastError(), "oed_eig");
 }
@@ -630,6 +720,7 @@ int oed_eig_designs(oed_ctx *ctx, const double *H_rec, int n, int nrec, int nwin
         return set_err(ctx, OED_EINVAL, "oed_eig_designs: bad arguments");
     for (int j = 0; j < kNT; j++)
         if (!(hi[j] > lo[j])) return set_err(ctx, OED_EINVAL, "oed_eig_designs: need hi > lo");
+    NvtxRange r("oed_eig_designs: per-design H, scaled Cholesky log-det, weighted sum");
     launch_eig_designs(H_rec, n, nrec, nwin, win, mask, ndesign, w, log_volume(lo, hi), eig, n_bad,
                        (cudaStream_t)stream);
     return cuda_err(ctx, cudaGetLastError(), "oed_eig_designs");

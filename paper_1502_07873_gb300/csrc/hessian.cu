@@ -59,17 +59,24 @@ __global__ void __launch_bounds__(512) k_hsub(const real *__restrict__ trace, Ge
                 for (int y = x; y < kNT; y++) acc[k++] += J[x] * J[y];
         }
     }
-    // per (r, c): sum over the lanes, then the two components of each receiver
-    extern __shared__ double sh[];   // [blockDim.x][29] (padded)
+    // the two components of a receiver sit in neighbouring threads of one warp (q = 2r + c
+    // and nq is even): a shuffle adds them (x + z, the order of the sum below), then the
+    // receiver's partial sums over the lanes are added in shared memory
+    const int wbase = t & ~31;
+    const int nact = min(32, (int)blockDim.x - wbase);
+    const unsigned mask = nact == 32 ? 0xffffffffu : ((1u << nact) - 1u);
 #pragma unroll
-    for (int k = 0; k < 28; k++) sh[t * 29 + k] = acc[k];
-    __syncthreads();
+    for (int k = 0; k < 28; k++) acc[k] += __shfl_xor_sync(mask, acc[k], 1);
+    extern __shared__ double sh[];   // [lanes][nrec][29] (padded)
     const int nrec = g.nrec;
+    if (mo < lanes && (q & 1) == 0)
+#pragma unroll
+        for (int k = 0; k < 28; k++) sh[(mo * nrec + (q >> 1)) * 29 + k] = acc[k];
+    __syncthreads();
     for (int w = t; w < nrec * 28; w += blockDim.x) {
         const int r = w / 28, k = w % 28;
         double v = 0.0;
-        for (int l = 0; l < lanes; l++)
-            v += sh[(l * nq + 2 * r) * 29 + k] + sh[(l * nq + 2 * r + 1) * 29 + k];
+        for (int l = 0; l < lanes; l++) v += sh[(l * nrec + r) * 29 + k];
         hsub[(((size_t)node * a.nsub + sub) * nrec + r) * 28 + k] = v;
     }
 }
@@ -160,7 +167,7 @@ void launch_hessian(const oed_ctx *ctx, int nnode, const double *inv2d, double s
     }
     a.nsub = nsub;
     const int threads = hsub_threads(g.nrec);
-    const size_t smem = (size_t)threads * 29 * sizeof(double);
+    const size_t smem = (size_t)(threads / 2) * 29 * sizeof(double);   // one row per (lane, receiver)
     dim3 grid(nnode, nsub);
     const bool diff = ctx->jac_mode != OED_JAC_PAIRS;   // one solve per parameter
     if (ctx->precision == OED_FP64) {

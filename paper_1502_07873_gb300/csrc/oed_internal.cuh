@@ -88,7 +88,8 @@ struct StepTuning {
     int zs;      // streaming kernel: rows marched per thread
     int wz;      // streaming kernel: warps along z in a block
     int C;       // > 0: cluster-resident kernel with clusters of C CTAs (FP32 only);
-                 // -1: TMA streaming kernel (FP32 only); 0: register streaming kernel
+                 // -1: TMA streaming kernel (FP32 only); -2: two-step TMA streaming
+                 // kernel (FP32, grids that do not fit on chip); 0: register streaming kernel
 };
 
 }  // namespace oed
@@ -110,6 +111,8 @@ struct oed_ctx {
                                // before every time loop, read when the Hessians are combined)
     void *d_u0 = nullptr;      // wavefield level buffer A [max_solves][2][nz][xp]
     void *d_u1 = nullptr;      // wavefield level buffer B
+    void *d_u2 = nullptr;      // second level pair of the two-step kernel (FP32 grids
+    void *d_u3 = nullptr;      // that do not fit on chip; NULL otherwise)
     void *d_src = nullptr;     // SourceDesc<real>[max_solves]
     void *d_stf = nullptr;     // real [max_solves][nsteps]
     void *d_trace = nullptr;   // real [max_solves][nlev][nrec][2]
@@ -120,6 +123,7 @@ struct oed_ctx {
     oed::StepTuning tune{4, 4, 0};
     int jac_mode = OED_JAC_PAIRS;   // Jacobian form of oed_hessian
     int tma_ctas = 0;               // persistent grid of the TMA streaming kernel
+    int tma2_ctas = 0;              // persistent grid of the two-step TMA kernel
     // host-path staging
     cudaStream_t own_stream = nullptr;
     double *h_stage_theta = nullptr, *h_stage_w = nullptr, *h_stage_H = nullptr,
@@ -149,8 +153,8 @@ inline int solves_per_node(const oed_ctx *ctx)
 void launch_rows(oed_ctx *ctx, cudaStream_t s);
 
 // stencil.cu
-void launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t s, cudaEvent_t ev0,
-                          cudaEvent_t ev1);
+cudaError_t launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t s, cudaEvent_t ev0,
+                                 cudaEvent_t ev1);
 void launch_trace_to_f64(const oed_ctx *ctx, int nsolve, double *g, cudaStream_t s);
 void launch_step_probe(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st, cudaEvent_t ev0,
                        cudaEvent_t ev1);
@@ -161,9 +165,17 @@ int tma_prepare(oed_ctx *ctx);
 cudaError_t launch_steps_tma(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0,
                              cudaEvent_t ev1, int nsteps_override);
 cudaError_t launch_wait_selftest(const oed_ctx *ctx, unsigned long long limit_ns, cudaStream_t st);
+void tma_record(cudaEvent_t ev, cudaStream_t st);
+cudaError_t launch_tma_one_step(const oed_ctx *ctx, int nsolve, cudaStream_t st, float *cur, float *nxt, int m);
+
+// stream_tma2.cu
+int tma2_prepare(oed_ctx *ctx);
+cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
+                              int nsteps_override, const float **last);
 
 // resident.cu
 int resident_cluster_size(const oed_ctx *ctx);
+int resident_fits(const Geometry &g);   // smallest cluster holding an FP32 grid, 0 if none
 int resident_max_active_clusters(const oed_ctx *ctx, int C);
 cudaError_t launch_resident(const oed_ctx *ctx, int C, int nsolve, cudaStream_t st, cudaEvent_t ev0,
                             cudaEvent_t ev1, int nsteps_override);

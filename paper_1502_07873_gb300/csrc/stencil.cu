@@ -223,23 +223,35 @@ void launch_step_probe(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st
 
 // Zero both level buffers (u^0 = u^{-1} = 0, Eq. elastic_2nd) and run all steps;
 // ev0 / ev1 (may be null) bracket the stencil launches.
-void launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0,
-                          cudaEvent_t ev1)
+cudaError_t launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0,
+                                 cudaEvent_t ev1)
 {
     const size_t bytes = (size_t)nsolve * ctx->g.solve_stride * ctx->elem;
     cudaMemsetAsync(ctx->d_u0, 0, bytes, st);
     cudaMemsetAsync(ctx->d_u1, 0, bytes, st);
+    if (ctx->tune.C == -2) {
+        cudaMemsetAsync(ctx->d_u2, 0, bytes, st);
+        cudaMemsetAsync(ctx->d_u3, 0, bytes, st);
+        const float *last = nullptr;
+        const cudaError_t e = launch_steps_tma2(ctx, nsolve, st, ev0, ev1, 0, &last);
+        if (e != cudaSuccess) return e;
+        k_gather<float><<<nsolve, 128, 0, st>>>(last, (float *)ctx->d_trace, ctx->d_rec, ctx->g, ctx->g.nsteps,
+                                                nsolve);
+        return cudaGetLastError();
+    }
     if (ctx->tune.C == -1) {
-        launch_steps_tma(ctx, nsolve, st, ev0, ev1, 0);
+        const cudaError_t e = launch_steps_tma(ctx, nsolve, st, ev0, ev1, 0);
+        if (e != cudaSuccess) return e;
         const float *last = (const float *)((ctx->g.nsteps & 1) ? ctx->d_u1 : ctx->d_u0);
         k_gather<float><<<nsolve, 128, 0, st>>>(last, (float *)ctx->d_trace, ctx->d_rec, ctx->g,
                                                 ctx->g.nsteps, nsolve);
-        return;
+        return cudaGetLastError();
     }
     if (ctx->precision == OED_FP64)
         launch_steps<double>(ctx, nsolve, st, ev0, ev1);
     else
         launch_steps<float>(ctx, nsolve, st, ev0, ev1);
+    return cudaGetLastError();
 }
 
 template <typename real>

@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include "stencil_cell.cuh"
+#include "tma_sync.cuh"
 
 namespace oed {
 
@@ -41,7 +42,6 @@ constexpr int kPlainBytes = kTX * kTZ * 4;               // 5120
 constexpr int kCoefBytes = kTZ * (int)sizeof(FacCoef<float>);   // 1280
 constexpr int kStageBytes = 2 * kHaloPad + 2 * kPlainBytes + kCoefBytes;
 constexpr unsigned kTileTxBytes = 2 * kHaloBytes + 2 * kPlainBytes;
-constexpr unsigned long long kWaitLimitNs = 2000000000ULL;   // 2 s per wait
 constexpr int kSmemBytes = kStages * kStageBytes + 128 /* alignment slack */ + 128 /* barriers */;
 
 struct TmaArgs {
@@ -56,51 +56,6 @@ struct TmaArgs {
     int m, nsolve, nbx, nbz;
 };
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bar)),
-                 "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                     (unsigned)__cvta_generic_to_shared(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((unsigned)__cvta_generic_to_shared(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// wait for the phase with the given parity, bounded by limit_ns; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
-                                          unsigned long long limit_ns = kWaitLimitNs)
-{
-    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        unsigned ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok)
-                     : "r"(a), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
-
 // Self-test of the bounded wait: one CTA waits for the first phase of a barrier that
 // expects one arrival and never gets it, so the wait can only end by its limit; it
 // then raises the same device flag as the streaming kernel does.
@@ -112,27 +67,6 @@ __global__ void k_wait_selftest(int *err, unsigned long long limit_ns)
     const bool ok = mbar_wait(&bar, 0, limit_ns);
     __syncthreads();
     if (threadIdx.x == 0 && !ok) atomicExch(err, 1);
-}
-
-__device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                          uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-            "r"((unsigned)__cvta_generic_to_shared(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z),
-        "r"((unsigned)__cvta_generic_to_shared(bar))
-        : "memory");
-}
-
-// 1-D bulk copy global -> shared, completion on an mbarrier (16-byte aligned, size a
-// multiple of 16)
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     (unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(bar))
-                 : "memory");
 }
 
 // stage and phase of the CTA's k-th tile: group k % kGroups takes it as its i-th
@@ -322,7 +256,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-static bool make_map(CUtensorMap *map, void *base, const Geometry &g, int nsolve, int bx, int bz)
+// Tensor map over the [2 nsolve][nz][xp] FP32 planes of one wavefield level, with
+// copy boxes of bx columns by bz rows.
+bool tma_make_map(CUtensorMap *map, void *base, const Geometry &g, int nsolve, int bx, int bz)
 {
     auto fn = encode_fn();
     if (!fn) return false;
@@ -363,14 +299,59 @@ int tma_prepare(oed_ctx *ctx)
     return ctx->tma_ctas;
 }
 
+// Record ev on st, as an external event node when st is being captured into a graph.
+void tma_record(cudaEvent_t ev, cudaStream_t st)
+{
+    if (!ev) return;
+    cudaStreamCaptureStatus cs;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
+
+static void tma_args(const oed_ctx *ctx, int nsolve, TmaArgs &a)
+{
+    a.fac = (const FacCoef<float> *)ctx->d_fac;
+    a.src = (const SourceDesc<float> *)ctx->d_src;
+    a.stf = (const float *)ctx->d_stf;
+    a.trace = (float *)ctx->d_trace;
+    a.rec = ctx->d_rec;
+    a.err = ctx->d_err;
+    a.g = ctx->g;
+    a.nsolve = nsolve;
+    a.nbx = (ctx->g.nx + kTX - 1) / kTX;
+    a.nbz = (ctx->g.nz + kTZ - 1) / kTZ;
+}
+
+// One step m of nsolve solves with the one-step kernel on explicit levels: u^m in cur,
+// u^{m-1} in nxt, overwritten with u^{m+1}.
+cudaError_t launch_tma_one_step(const oed_ctx *ctx, int nsolve, cudaStream_t st, float *cur, float *nxt, int m)
+{
+    CUtensorMap halo, plain;
+    if (!tma_make_map(&halo, cur, ctx->g, nsolve, kWX, kWZ) || !tma_make_map(&plain, nxt, ctx->g, nsolve, kTX, kTZ))
+        return cudaErrorInvalidValue;
+    if (ctx->tma_ctas < 1) return cudaErrorInvalidConfiguration;
+    TmaArgs a;
+    tma_args(ctx, nsolve, a);
+    const long long ntile = (long long)nsolve * a.nbx * a.nbz;
+    if (ntile >= (1LL << 31) - 2LL * ctx->tma_ctas) return cudaErrorInvalidValue;
+    const int grid = (int)(ntile < (long long)ctx->tma_ctas ? ntile : (long long)ctx->tma_ctas);
+    a.nxt = nxt;
+    a.m = m;
+    k_step_tma<<<grid, 32 * (kConsumerWarps + 1), kSmemBytes, st>>>(a, halo, plain);
+    return cudaGetLastError();
+}
+
 // All steps of nsolve solves with the TMA kernel (the caller zeroes the levels).
 cudaError_t launch_steps_tma(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0,
                              cudaEvent_t ev1, int nsteps_override)
 {
     const Geometry &g = ctx->g;
     CUtensorMap halo0, halo1, plain0, plain1;
-    if (!make_map(&halo0, ctx->d_u0, g, nsolve, kWX, kWZ) || !make_map(&halo1, ctx->d_u1, g, nsolve, kWX, kWZ) ||
-        !make_map(&plain0, ctx->d_u0, g, nsolve, kTX, kTZ) || !make_map(&plain1, ctx->d_u1, g, nsolve, kTX, kTZ))
+    if (!tma_make_map(&halo0, ctx->d_u0, g, nsolve, kWX, kWZ) || !tma_make_map(&halo1, ctx->d_u1, g, nsolve, kWX, kWZ) ||
+        !tma_make_map(&plain0, ctx->d_u0, g, nsolve, kTX, kTZ) || !tma_make_map(&plain1, ctx->d_u1, g, nsolve, kTX, kTZ))
         return cudaErrorInvalidValue;
     const int smem = kSmemBytes;
     if (ctx->tma_ctas < 1) return cudaErrorInvalidConfiguration;

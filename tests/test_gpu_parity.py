@@ -434,7 +434,8 @@ def test_nodes_mc_matches_oracle(P, oracle):
 @pytest.mark.slow
 def test_full_size_batched_sampled(P, oracle):
     """401x201 grid, 2000 steps, 256 nodes x 15 solves in one launch configuration (the
-    benchmark's): sampled seismograms and a sampled node's gain against the oracle."""
+    benchmark's): sampled seismograms and the gains of ten nodes spread over the prior box
+    against the oracle (the mixed-precision bar, 1e-3)."""
     w = W.batched()
     th, wt = oracle.mc_nodes(w.uniforms(), w.prior_lo, w.prior_hi)
     sigma = 0.5
@@ -450,11 +451,20 @@ def test_full_size_batched_sampled(P, oracle):
     assert int(nb.item()) == 0
     G = oracle.Grid.from_workload(w)
     lp = oracle.log_uniform_density(w.prior_lo, w.prior_hi)
-    for i in (0, 137):
+    # ten nodes spread over the prior box: nodes 0 and 1, then the nodes nearest both ends
+    # of the x_s, z_s, t_s and omega_s intervals (a late, low-frequency source gives the
+    # smallest signal and the largest FP32 cancellation in the pairs Jacobian)
+    sample = W.spread_sample(th, w.prior_lo, w.prior_hi)
+    assert len(sample) == 10
+    d_gpu = dkl.cpu().numpy()
+    errs = []
+    for i in sample:
         Href, _ = oracle.node_hessian(G, th[i], w.prior_lo, w.prior_hi, w.rel_step, sigma)
         ld, _, ok = oracle.scaled_logdet(Href)
+        assert ok
         d_ref = oracle.dkl(ld, 7, lp)
-        assert abs(float(dkl[i].item()) - d_ref) <= 1e-3 * abs(d_ref), (i, float(dkl[i].item()), d_ref)
+        errs.append((abs(d_gpu[i] - d_ref) / abs(d_ref), i, d_gpu[i], d_ref))
+    assert max(errs)[0] <= 1e-3, max(errs)
     # seismograms of two solves of the same launch shape
     g = torch.empty((2, w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
     P.oed_forward(ctx, _t(th[[5, 200]]), g)

@@ -140,6 +140,22 @@ def design_subsets(nrec: int = 40, kmax: int = 10, per_k: int = 512, seed: int =
     return masks
 
 
+def spread_sample(theta: np.ndarray, lo, hi, first=(0, 1), params=(0, 1, 2, 3)) -> List[int]:
+    """Indices of nodes spread over the prior box, for sampled checks of a batch: the
+    nodes in `first`, then for each parameter in `params` (default x_s, z_s, t_s,
+    omega_s) the node nearest the low end and the node nearest the high end of its
+    prior interval, skipping repeats (up to len(first) + 2 len(params) nodes)."""
+    u = (np.asarray(theta) - np.asarray(lo)) / (np.asarray(hi) - np.asarray(lo))
+    out = [int(i) for i in first if 0 <= int(i) < u.shape[0]]
+    for j in params:
+        for order in (np.argsort(u[:, j], kind="stable"), np.argsort(-u[:, j], kind="stable")):
+            for i in order:
+                if int(i) not in out:
+                    out.append(int(i))
+                    break
+    return out
+
+
 SERVING_GRIDS = ((201, 101, 10.0), (401, 201, 5.0), (801, 401, 2.5), (1601, 801, 1.25))
 
 
