@@ -610,6 +610,8 @@ def measure_layered(P, torch, dev, args, rank, oracle_nodes=2):
     w = W.layered()
     sigma = args.sigma if args.sigma > 0 else noise_sigma_gpu(P, torch, w, P.OED_FP32)
     x, wt = P.oed_nodes_smolyak(7, w.smolyak_level, w.prior_lo, w.prior_hi)
+    if args.nodes:   # profiling runs: the first nodes of the rule only
+        x, wt = x[:args.nodes], wt[:args.nodes]
     chunk_nodes = 96
     n = x.shape[0]
     ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=7 * chunk_nodes)
@@ -625,7 +627,7 @@ def measure_layered(P, torch, dev, args, rank, oracle_nodes=2):
     nb = torch.empty(1, dtype=torch.int32, device=dev)
     # warm-up: one full chunk and the last, partial one (their captured time loops)
     tail = n - (n // chunk_nodes) * chunk_nodes
-    warm = list(range(chunk_nodes)) + list(range(n - tail, n))
+    warm = list(range(min(chunk_nodes, n))) + (list(range(n - tail, n)) if tail and n > chunk_nodes else [])
     P.oed_hessian(ctx, theta[warm], w.prior_lo, w.prior_hi, w.rel_step, sigma, H[:len(warm)], stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -76,7 +76,7 @@ static Geometry make_geometry(const oed_problem *p)
 }
 
 struct Sizes {
-    size_t u, u2, src, stf, trace, theta, rows, rec, hseg, err, total;
+    size_t u, u2, kp, src, stf, trace, theta, rows, rec, hseg, err, total;
 };
 
 static Sizes sizes(const Geometry &g, int precision, int max_solves)
@@ -89,6 +89,7 @@ static Sizes sizes(const Geometry &g, int precision, int max_solves)
     // FP32 grids that do not fit on chip keep a second pair of levels for the two-step
     // kernel (it reads one pair and writes the other)
     s.u2 = (precision == OED_FP32 && !resident_fits(g)) ? 2 * s.u : 0;
+    s.kp = s.u2 ? al((size_t)g.nz * 16 * sizeof(float)) : 0;   // packed row coefficients
     s.src = al((size_t)max_solves * (precision == OED_FP64 ? sizeof(SourceDesc<double>)
                                                            : sizeof(SourceDesc<float>)));
     s.stf = al((size_t)max_solves * g.nsteps * e);
@@ -99,7 +100,7 @@ static Sizes sizes(const Geometry &g, int precision, int max_solves)
     s.rec = al((size_t)g.nrec * sizeof(int));
     s.hseg = al((size_t)chunk * 16 * g.nrec * 28 * sizeof(double));
     s.err = 256;
-    s.total = 2 * s.u + s.u2 + s.src + s.stf + s.trace + s.theta + s.rows + s.rec + s.hseg + s.err;
+    s.total = 2 * s.u + s.u2 + s.kp + s.src + s.stf + s.trace + s.theta + s.rows + s.rec + s.hseg + s.err;
     return s;
 }
 
@@ -161,6 +162,8 @@ static void carve(oed_ctx *ctx, char *base, const Sizes &s)
     ctx->d_u2 = s.u2 ? q : nullptr;
     ctx->d_u3 = s.u2 ? q + s.u : nullptr;
     q += s.u2;
+    ctx->d_kp = s.kp ? q : nullptr;
+    q += s.kp;
     ctx->d_src = q; q += s.src;
     ctx->d_stf = q; q += s.stf;
     ctx->d_trace = q; q += s.trace;
@@ -187,6 +190,7 @@ static void fill_problem(oed_ctx *ctx)
     cudaMemcpyAsync(ctx->d_rec, ctx->rec_ix.data(), sizeof(int) * ctx->rec_ix.size(), cudaMemcpyHostToDevice,
                     ctx->own_stream);
     launch_rows(ctx, ctx->own_stream);   // synchronises the stream
+    launch_pack_kp(ctx, ctx->own_stream);
 }
 
 }  // namespace oed

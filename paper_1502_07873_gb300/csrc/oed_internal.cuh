@@ -113,6 +113,7 @@ struct oed_ctx {
     void *d_u1 = nullptr;      // wavefield level buffer B
     void *d_u2 = nullptr;      // second level pair of the two-step kernel (FP32 grids
     void *d_u3 = nullptr;      // that do not fit on chip; NULL otherwise)
+    void *d_kp = nullptr;      // [nz] the rows' coefficients as (x, z) pairs (two-step kernel)
     void *d_src = nullptr;     // SourceDesc<real>[max_solves]
     void *d_stf = nullptr;     // real [max_solves][nsteps]
     void *d_trace = nullptr;   // real [max_solves][nlev][nrec][2]
@@ -170,6 +171,7 @@ cudaError_t launch_tma_one_step(const oed_ctx *ctx, int nsolve, cudaStream_t st,
 
 // stream_tma2.cu
 int tma2_prepare(oed_ctx *ctx);
+void launch_pack_kp(const oed_ctx *ctx, cudaStream_t st);
 cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
                               int nsteps_override, const float **last);
 

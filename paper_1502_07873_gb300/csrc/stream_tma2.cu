@@ -7,13 +7,15 @@
 // shared-memory ring:
 //   HM  u^m,     x and z planes, rows z0-2 .. z0+21, columns x0-4 .. x0+63
 //   HP  u^{m-1}, x and z planes, rows z0-1 .. z0+20, columns x0-4 .. x0+63
-// and, with cp.async.bulk, the coefficient rows z0-1 .. z0+20 that lie in the grid
+// and, with cp.async.bulk, the coefficient rows z0-1 .. z0+20 that lie in the grid, as
+// (x, z) pairs packed once per problem
 // (x0 is a multiple of 60, so every x start is a multiple of four floats and every
 // copy starts on a 16-byte boundary; rows and columns outside the grid read as
 // zeros and are never used).  Completion is tracked per stage by an mbarrier with
 // the stage's byte count.  Two groups of four consumer warps take the tiles in turn,
 // each owning two stages.  In a tile, lane p owns the column pair x0-2+2p and a warp
-// a segment of rows:
+// a segment of rows (the tests for the surface and bottom rows, the side columns and
+// the source patch run only in the tiles that hold them):
 //   step 1  u^{m+1} on rows z0-1 .. z0+20, columns x0-2 .. x0+61 (the tile and a
 //           one-node ring), written in place over u^{m-1} in HP (a node reads only
 //           its own u^{m-1}), and, for the tile's own nodes, to global memory;
@@ -44,18 +46,19 @@ constexpr int k2GroupWarps = 4, k2ConsumerWarps = k2Groups * k2GroupWarps;
 constexpr int k2PlaneM = kW2X * kM2Z * 4;                       // 6528 = 51 x 128
 constexpr int k2PlaneP = kW2X * kP2Z * 4;                       // 5984
 constexpr int k2PlanePPad = (k2PlaneP + 127) / 128 * 128;       // 6016
-constexpr int k2Coef = kP2Z * (int)sizeof(FacCoef<float>);      // 1408
+constexpr int k2Coef = kP2Z * (int)sizeof(KP);                  // 1408
 constexpr int k2StageBytes = 2 * k2PlaneM + 2 * k2PlanePPad + k2Coef;
 constexpr unsigned k2TileTx = 2 * k2PlaneM + 2 * k2PlaneP;
 constexpr int k2SmemBytes = k2Stages * k2StageBytes + 128 /* alignment slack */ + 128 /* barriers */;
 // rows of step 1 per warp (22 = 6 + 6 + 5 + 5) and of step 2 (20 = 4 x 5)
 __device__ __constant__ int k2Seg1[k2GroupWarps + 1] = {0, 6, 12, 17, 22};
+constexpr int k2Seg1Max = 6;
 constexpr int k2Rows2 = kT2Z / k2GroupWarps;
 
 struct Tma2Args {
     float *outA;                  // u^{m+1} (global, the other pair's older level)
     float *outB;                  // u^{m+2} (global, the other pair's newer level)
-    const FacCoef<float> *fac;
+    const KP *kp;                 // [nz] the rows' coefficients as (x, z) pairs
     const SourceDesc<float> *src;
     const float *stf;
     float *trace;
@@ -102,26 +105,34 @@ __device__ __forceinline__ void plane_put(float *px, float *pz, int r, int q, fl
 struct PairCtx {
     int kind;          // side-column flags (stencil_cell.cuh)
     int siA, siB;      // column offsets in the source patch
+    int j0;            // first row of the source patch
     bool scolA, scolB; // the pair's columns lie in the patch
 };
 
+struct TileFlags {
+    bool rows;   // the surface or the bottom row is among the tile's rows
+    bool side;   // a side column is among the tile's columns
+    bool src;    // the source patch meets the tile
+};
+
 __device__ __forceinline__ void update_at(const KP &K, int z, int nz, const Row2P &rn, const Row2P &rc,
-                                          const Row2P &rs, const PairCtx &pc, const SourceDesc<float> *sd,
-                                          float S, float4 &u)
+                                          const Row2P &rs, const PairCtx &pc, const TileFlags &tf,
+                                          const SourceDesc<float> *sd, float S, float4 &u)
 {
-    if (z == nz - 1) {
+    if (tf.rows && z == nz - 1) {
         absorbingP(K.c, make_float4(rn.ca.x, rn.ca.y, rn.cb.x, rn.cb.y), rc, true, pc.kind, u);
-    } else if (z == 0) {   // surface row: no north differences, cross terms on the row itself
+    } else if (tf.rows && z == 0) {   // surface row: no north differences, cross terms on the row itself
         Row2P nt = rc;
         nt.va = nt.vb = make_float2(0.0f, 0.0f);
         pair_updateP(K, nt, rc, rs, u);
         if (pc.kind) absorbingP(K.c, u, rc, false, pc.kind, u);
     } else {
         pair_updateP(K, rn, rc, rs, u);
-        if (pc.kind) absorbingP(K.c, u, rc, false, pc.kind, u);
+        if (tf.side && pc.kind) absorbingP(K.c, u, rc, false, pc.kind, u);
     }
-    const int b = z - sd->j0;
-    if ((unsigned)b < (unsigned)kPatch) {
+    if (!tf.src) return;
+    const int b = z - pc.j0;
+    if ((unsigned)b < (unsigned)kPatch && (pc.scolA || pc.scolB)) {
         if (pc.scolA) {
             u.x = add_force(u.x, S, sd->wx[b * kPatch + pc.siA]);
             u.y = add_force(u.y, S, sd->wz[b * kPatch + pc.siA]);
@@ -190,14 +201,14 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
                 unsigned char *st = smem + stage * k2StageBytes;
                 // coefficient rows z0-1 .. z0+20 inside the grid
                 const int c0 = max(0, z0 - 1), c1 = min(g.nz, z0 + kT2Z + 1);
-                const unsigned cbytes = (unsigned)((c1 - c0) * (int)sizeof(FacCoef<float>));
+                const unsigned cbytes = (unsigned)((c1 - c0) * (int)sizeof(KP));
                 mbar_expect_tx(&full_bar[stage], k2TileTx + cbytes);
                 tma_load3(st, &cur_m, x0 - 4, z0 - 2, 2 * s, &full_bar[stage]);
                 tma_load3(st + k2PlaneM, &cur_m, x0 - 4, z0 - 2, 2 * s + 1, &full_bar[stage]);
                 tma_load3(st + 2 * k2PlaneM, &cur_p, x0 - 4, z0 - 1, 2 * s, &full_bar[stage]);
                 tma_load3(st + 2 * k2PlaneM + k2PlanePPad, &cur_p, x0 - 4, z0 - 1, 2 * s + 1, &full_bar[stage]);
-                bulk_load(st + 2 * k2PlaneM + 2 * k2PlanePPad + (c0 - (z0 - 1)) * (int)sizeof(FacCoef<float>),
-                          a.fac + c0, cbytes, &full_bar[stage]);
+                bulk_load(st + 2 * k2PlaneM + 2 * k2PlanePPad + (c0 - (z0 - 1)) * (int)sizeof(KP), a.kp + c0,
+                          cbytes, &full_bar[stage]);
             }
             if (!ok) {
                 atomicExch(a.err, 1);
@@ -231,7 +242,20 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
         const float *hmz = hmx + k2PlaneM / 4;
         float *hpx = reinterpret_cast<float *>(st + 2 * k2PlaneM);
         float *hpz = hpx + k2PlanePPad / 4;
-        const FacCoef<float> *cf = reinterpret_cast<const FacCoef<float> *>(st + 2 * k2PlaneM + 2 * k2PlanePPad);
+        const KP *kp = reinterpret_cast<const KP *>(st + 2 * k2PlaneM + 2 * k2PlanePPad);
+        const SourceDesc<float> *sd = a.src + s;
+        float *gAx = a.outA + (size_t)s * g.solve_stride, *gAz = gAx + g.comp_stride;
+        float *gBx = a.outB + (size_t)s * g.solve_stride, *gBz = gBx + g.comp_stride;
+        const int c = x0 - 2 + 2 * lane;   // the pair's first column
+        const int si0 = sd->i0, sj0 = sd->j0;
+        // tile-uniform flags: the tile (with its ring) holds the surface or bottom row, a
+        // side column, or part of the source patch; the tests of each are skipped
+        // elsewhere, which is most tiles
+        TileFlags tf;
+        tf.rows = z0 < 2 || z0 + kT2Z > g.nz - 2;
+        tf.side = x0 < 3 || x0 + kT2X + 1 > g.nx - 2;
+        tf.src = !(sj0 + kPatch <= z0 - 1 || sj0 >= z0 + kT2Z + 1 || si0 + kPatch <= x0 - 2 ||
+                   si0 >= x0 + kT2X + 2);
         const size_t tr0 = (size_t)s * g.nlev * g.nrec * 2;
         // receiver samples of level m (HM row 2 is grid row 0 on the surface band)
         if (z0 == 0)
@@ -240,35 +264,37 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
                 if (xr >= 0 && xr < kT2X)
                     a.trace[tr0 + (size_t)a.m * g.nrec * 2 + r] = ((r & 1) ? hmz : hmx)[2 * kW2X + xr + 4];
             }
-        const int c = x0 - 2 + 2 * lane;   // the pair's first column
         const bool valid = c >= 0 && c < g.nx;
         PairCtx pc;
         pc.kind = (c == 0 ? 1 : 0) | (c + 1 == g.nx - 1 ? 2 : 0) | (c == g.nx - 1 ? 4 : 0);
-        const SourceDesc<float> *sd = a.src + s;
-        pc.siA = c - sd->i0;
-        pc.siB = c + 1 - sd->i0;
+        pc.siA = c - si0;
+        pc.siB = c + 1 - si0;
+        pc.j0 = sj0;
         pc.scolA = (unsigned)pc.siA < (unsigned)kPatch;
         pc.scolB = c + 1 < g.nx && (unsigned)pc.siB < (unsigned)kPatch;
         const bool own = lane >= 1 && lane <= kT2X / 2 && valid;   // a pair of the tile itself
-        float *gAx = a.outA + (size_t)s * g.solve_stride, *gAz = gAx + g.comp_stride;
-        float *gBx = a.outB + (size_t)s * g.solve_stride, *gBz = gBx + g.comp_stride;
         const float S1 = (pc.scolA || pc.scolB) ? a.stf[(size_t)s * g.nsteps + a.m] : 0.0f;
         const float S2 = (pc.scolA || pc.scolB) && a.m + 1 < g.nsteps ? a.stf[(size_t)s * g.nsteps + a.m + 1] : 0.0f;
 
         // step 1: u^{m+1} on HP rows [r_a, r_b) (grid row z0 - 1 + r)
         if (valid) {
-            const int ra = k2Seg1[wig], rb = k2Seg1[wig + 1];
+            const int ra = k2Seg1[wig], nr = k2Seg1[wig + 1] - ra;
             Row2P rn, rc, rs;
             plane_row(hmx, hmz, ra, q, rn);       // HM row r is grid row z0 - 2 + r
             plane_row(hmx, hmz, ra + 1, q, rc);
             southP(rn, rc);
-            for (int r = ra; r < rb; r++) {
+            // unrolled to the longest segment, so the window rows stay in place in the
+            // registers instead of being copied row after row
+#pragma unroll
+            for (int i = 0; i < k2Seg1Max; i++) {
+                if (i >= nr) break;
+                const int r = ra + i;
                 const int z = z0 - 1 + r;
                 plane_row(hmx, hmz, r + 2, q, rs);
                 southP(rc, rs);
                 if (z >= 0 && z < g.nz) {
                     float4 u = plane_pair(hpx, hpz, r, q);
-                    update_at(pack_coef(cf[r]), z, g.nz, rn, rc, rs, pc, sd, S1, u);
+                    update_at(kp[r], z, g.nz, rn, rc, rs, pc, tf, sd, S1, u);
                     plane_put(hpx, hpz, r, q, u);
                     if (own && r >= 1 && r <= kT2Z) {
                         const size_t o = (size_t)z * g.xp + c;
@@ -302,7 +328,7 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
                 plane_row(hpx, hpz, r + 2, q, rs);
                 southP(rc, rs);
                 float4 u = plane_pair(hmx, hmz, r + 2, q);   // u^m of the node
-                update_at(pack_coef(cf[r + 1]), z, g.nz, rn, rc, rs, pc, sd, S2, u);
+                update_at(kp[r + 1], z, g.nz, rn, rc, rs, pc, tf, sd, S2, u);
                 const size_t o = (size_t)z * g.xp + c;
                 __stcs(reinterpret_cast<float2 *>(gBx + o), make_float2(u.x, u.z));
                 __stcs(reinterpret_cast<float2 *>(gBz + o), make_float2(u.y, u.w));
@@ -315,7 +341,21 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
     }
 }
 
+// The rows' coefficients as (x, z) pairs, the form the packed update reads.
+__global__ void k_pack_kp(const FacCoef<float> *__restrict__ fac, int nz, KP *__restrict__ kp)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nz) kp[j] = pack_coef(fac[j]);
+}
+
 // ---------------------------------------------------------------- host side
+
+void launch_pack_kp(const oed_ctx *ctx, cudaStream_t st)
+{
+    if (!ctx->d_kp) return;
+    k_pack_kp<<<(ctx->g.nz + 127) / 128, 128, 0, st>>>((const FacCoef<float> *)ctx->d_fac, ctx->g.nz,
+                                                       (KP *)ctx->d_kp);
+}
 
 int tma2_prepare(oed_ctx *ctx)
 {
@@ -340,7 +380,7 @@ cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, c
                               int nsteps_override, const float **last)
 {
     const Geometry &g = ctx->g;
-    if (ctx->tma2_ctas < 1 || !ctx->d_u2) return cudaErrorInvalidConfiguration;
+    if (ctx->tma2_ctas < 1 || !ctx->d_u2 || !ctx->d_kp) return cudaErrorInvalidConfiguration;
     float *lv[4] = {(float *)ctx->d_u0, (float *)ctx->d_u1, (float *)ctx->d_u2, (float *)ctx->d_u3};
     CUtensorMap mmap[2], pmap[2];   // per pair: u^m (newer level, 2-row halo), u^{m-1} (older, 1-row)
     for (int pr = 0; pr < 2; pr++)
@@ -348,7 +388,7 @@ cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, c
             !tma_make_map(&pmap[pr], lv[2 * pr], g, nsolve, kW2X, kP2Z))
             return cudaErrorInvalidValue;
     Tma2Args a;
-    a.fac = (const FacCoef<float> *)ctx->d_fac;
+    a.kp = (const KP *)ctx->d_kp;
     a.src = (const SourceDesc<float> *)ctx->d_src;
     a.stf = (const float *)ctx->d_stf;
     a.trace = (float *)ctx->d_trace;

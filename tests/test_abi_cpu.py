@@ -181,3 +181,42 @@ def test_struct_mirrors_match_the_c_layout(P, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_workspace_holds_two_level_pairs_off_chip(P):
+    """FP32 grids that do not fit on chip reserve a second pair of levels (the two-step
+    kernel reads one pair and writes the other); FP32 grids that fit, and FP64, do not."""
+    w = W.layered()                     # 801x401: does not fit on chip
+    n = 700
+    level32 = n * 2 * w.nz * 832 * 4    # one FP32 level (two components, padded rows)
+    f32 = P.oed_workspace_bytes(P.problem_from_workload(w, P.OED_FP32), n)
+    f64 = P.oed_workspace_bytes(P.problem_from_workload(w, P.OED_FP64), n)
+    assert 4 * level32 < f32 < 4 * level32 * 1.2
+    assert 4 * level32 < f64 < 4 * level32 * 1.3   # two FP64 levels (and 8-byte traces)
+    b = W.batched()                     # 401x201 fits on chip: one pair
+    fb = P.oed_workspace_bytes(P.problem_from_workload(b, P.OED_FP32), n)
+    assert 2 * n * 2 * b.nz * 416 * 4 < fb < 3 * n * 2 * b.nz * 416 * 4
+
+
+def test_server_host_side_sizing_and_validation(P):
+    """The server's footprint rule and submission checks run on the host: a request
+    reserves a workspace for chunks of chunk_nodes nodes plus its arrays; a resume with
+    more finished nodes than the request, or without their Hessians, is refused."""
+    import numpy as np
+    w = W.tiny(nx=61, nz=31, h=33.0, nsteps=40, nrec=3)
+    n = 10
+    rng = np.random.default_rng(3)
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+    th = lo + (hi - lo) * rng.random((n, 7))
+    prob = P.problem_from_workload(w, P.OED_FP32)
+    r = P.make_request(prob, th, np.full(n, 0.1), w.prior_lo, w.prior_hi, w.rel_step, 0.1, P.OED_JAC_DIFFERENCE)
+    L = P.library()
+    b = L.oed_server_request_bytes(ctypes.byref(r), 4)
+    assert b == P.oed_workspace_bytes(prob, 7 * 4) + n * 57 * 8 + 4096
+    assert L.oed_server_request_bytes(ctypes.byref(r), 100) == P.oed_workspace_bytes(prob, 7 * n) + n * 57 * 8 + 4096
+    with pytest.raises(ValueError):
+        P.make_request(prob, th, np.full(n, 0.1), w.prior_lo, w.prior_hi, w.rel_step, 0.1, 1,
+                       H_done=np.zeros((n + 1, 7, 7)))
+    r.n_done = 3   # finished nodes without their Hessians
+    rid = ctypes.c_ulonglong()
+    assert L.oed_server_submit(None, ctypes.byref(r), ctypes.byref(rid)) == P.OED_EINVAL

@@ -5,7 +5,8 @@ Hessians over the 91 candidate surface nodes from sensitivity solves (Alg. 1 ste
 FP32 stencil.  Checks: H_1 at the prior mean against the oracle and the conditioning the
 paper prints (3.88e30 -> 12.16); the shape of Scenarios I-III: EIG grows with the number
 of receivers on a fixed aperture (I) and at fixed spacing (II), and a five-receiver array
-has an interior optimum spacing (III; the paper finds 1000 m).
+has an interior optimum spacing on a flat top, 1000 .. 1800 m, with the paper's 1000 m
+within 0.3% of the best (III).
 """
 import numpy as np
 import pytest
@@ -69,9 +70,15 @@ def test_scenarios_shape(P):
     assert all(np.diff(s1) > 0) and all(np.diff(s2) > 0)
     # diminishing returns in Scenario I beyond ~17-20 receivers
     assert (s1[3] - s1[2]) / 8 > (s1[5] - s1[4]) / 40
-    best = max(s3, key=lambda t: t[1])[0]
-    assert 600 <= best <= 2400, s3                       # paper: 1000 m
-    assert s3[0][1] < max(x for _, x in s3) and s3[-1][1] < max(x for _, x in s3)
+    # Scenario III: an interior optimum on a flat top.  On this model the sparse grid of
+    # 8583 nodes and 10^4 Monte Carlo nodes both put it at 1400 m, with the paper's 1000 m
+    # within 0.15% of the maximum and every spacing in 1000 .. 1800 m within 0.2%; the
+    # array of 200 m (too short) and 4000 m (too wide) spacing are clearly below
+    best, top = max(s3, key=lambda t: t[1])
+    assert 1000 <= best <= 1800, s3                      # paper: 1000 m
+    at = dict(s3)
+    assert at[1000] >= top * (1 - 3e-3), s3
+    assert at[200] < top * (1 - 1e-2) and at[4000] < top * (1 - 1e-2), s3
     # the union of candidates at fixed spacing 1000 m: Scenario I (17 receivers, 1000 m)
     # and Scenario II (17 receivers) are the same design
     assert by["I"][3][1] == pytest.approx(by["II"][8][1], rel=1e-12)
