@@ -31,6 +31,14 @@ __device__ __forceinline__ KP pack_coef(const FacCoef<float> &f)
     return k;
 }
 
+// the coefficients that the update and the absorbing rows read are equal
+__device__ __forceinline__ bool kp_equal(const KP &a, const KP &b)
+{
+    return a.a.x == b.a.x && a.a.y == b.a.y && a.vs.x == b.vs.x && a.vs.y == b.vs.y && a.vn.x == b.vn.x &&
+           a.vn.y == b.vn.y && a.ds.x == b.ds.x && a.ds.y == b.ds.y && a.dn.x == b.dn.x && a.dn.y == b.dn.y &&
+           a.c.x == b.c.x && a.c.y == b.c.y;
+}
+
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 // a - b as one rounding: b * (-1) is exact, so fma(b, -1, a) rounds a - b once

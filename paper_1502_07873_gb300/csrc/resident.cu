@@ -177,6 +177,15 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     // the warps that hold a side column run the march with the absorbing patch, the
     // others (most of them) a march without it
     const bool warp_side = __any_sync(0xffffffffu, active && kind != 0);
+    // when every row the march visits in this CTA (rows 1 or 0 .. nrows-2: the surface and
+    // the last row are peeled) has the coefficients of the first, as in a homogeneous
+    // medium, the march keeps them in registers instead of reloading them row by row
+    const int kfirst = (j0 == 0) ? 1 : 0;
+    __syncthreads();
+    bool same = true;
+    for (int k = kfirst + 1 + tid; k < nrows - 1; k += nthr) same &= kp_equal(coef[k], coef[kfirst]);
+    const bool unif = __syncthreads_and(same) != 0 && kfirst < nrows - 1;
+    const KP K0 = coef[min(kfirst, nrows - 1)];
     cluster_barrier();
 
     for (int m = 0; m < g.nsteps; m++) {
@@ -228,7 +237,8 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 float2 pe = sp[1];
                 // side: the warp holds a side column (absorbing patch compiled in);
                 // pf: a row below the south row exists, prefetch it (every row but the last)
-                auto march = [&](auto side) {
+                // unifK: the CTA's march rows share K0 (no coefficient loads)
+                auto march = [&](auto side, auto unifK) {
                     auto row = [&](auto pf, const Row2P &wn, Row2P &wc, Row2P &ws) {
                         row_fromP(pw, pm, pe, ws);
                         float4 u = pu;
@@ -240,7 +250,7 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                             pu = pair_at(o + RS, sq);
                         }
                         southP(wc, ws);
-                        const KP K = *cf;
+                        const KP K = decltype(unifK)::value ? K0 : *cf;
                         pair_updateP(K, wn, wc, ws, u);
                         if constexpr (decltype(side)::value) {
                             if (kind) absorbingP(K.c, u, wc, false, kind, u);
@@ -278,10 +288,17 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 };
                 // a warp-uniform choice: a branch inside the march body would split the
                 // unrolled rows into separate blocks and cost the scheduler its overlap
-                if (warp_side)
-                    march(std::true_type{});
-                else
-                    march(std::false_type{});
+                if (warp_side) {
+                    if (unif)
+                        march(std::true_type{}, std::true_type{});
+                    else
+                        march(std::true_type{}, std::false_type{});
+                } else {
+                    if (unif)
+                        march(std::false_type{}, std::true_type{});
+                    else
+                        march(std::false_type{}, std::false_type{});
+                }
             }
             // what is left: a last interior row whose south neighbour sits in CTA rank+1,
             // or the absorbing bottom row

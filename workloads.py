@@ -244,11 +244,12 @@ def paper_study_model() -> Workload:
                     layers=w.layers, rec_ix=[5, 55], prior_lo=w.prior_lo, prior_hi=w.prior_hi)
 
 
-def paper_study_thetas(u: np.ndarray) -> np.ndarray:
-    """Full parameter vectors from uniform variates u[n][3] of the three unknowns."""
+def paper_study_thetas(u: np.ndarray, unknown=PAPER_STUDY_UNKNOWN) -> np.ndarray:
+    """Full parameter vectors from uniform variates u[n][len(unknown)] of the unknowns (the
+    others take their known values)."""
     lo, hi = np.array(PAPER_PRIOR_LO), np.array(PAPER_PRIOR_HI)
     th = np.tile(np.array(PAPER_STUDY_KNOWN), (u.shape[0], 1))
-    for k, j in enumerate(PAPER_STUDY_UNKNOWN):
+    for k, j in enumerate(unknown):
         th[:, j] = lo[j] + (hi[j] - lo[j]) * u[:, k]
     return th
 
