@@ -220,3 +220,18 @@ def test_server_host_side_sizing_and_validation(P):
     r.n_done = 3   # finished nodes without their Hessians
     rid = ctypes.c_ulonglong()
     assert L.oed_server_submit(None, ctypes.byref(r), ctypes.byref(rid)) == P.OED_EINVAL
+
+
+def test_spread_sample_takes_both_ends_of_each_interval():
+    """The node picker of the sampled checks: the given nodes first, then for x_s, z_s, t_s
+    and omega_s the node nearest each end of its prior interval, without repeats."""
+    import numpy as np
+    w = W.batched()
+    lo, hi = np.array(w.prior_lo), np.array(w.prior_hi)
+    th = lo + (hi - lo) * w.uniforms()
+    idx = W.spread_sample(th, w.prior_lo, w.prior_hi)
+    assert idx[:2] == [0, 1] and len(idx) == len(set(idx)) == 10
+    u = (th - lo) / (hi - lo)
+    for j in range(4):
+        assert int(np.argmin(u[:, j])) in idx or np.argmin(u[:, j]) in (0, 1)
+        assert int(np.argmax(u[:, j])) in idx or np.argmax(u[:, j]) in (0, 1)

@@ -238,6 +238,11 @@ def test_cancel_then_resume_from_the_checkpoint_gives_the_same_eig(P):
     m = srv.metrics(3)
     assert m["nodes_resumed"] == k and m["tag"] == 8
     assert m["cell_updates"] == w.nx * w.nz * w.nsteps * 15 * (n - k)
+    # resuming with every node done computes no solve: the EIG comes from the checkpoint
+    res_all = srv.wait(srv.submit(P.make_request(prob, th, wt, w.prior_lo, w.prior_hi, w.rel_step, 0.05,
+                                                 P.OED_JAC_PAIRS, H_done=H_full)))
+    assert res_all.status == P.OED_OK and res_all.eig == full.eig
+    assert srv.metrics(4)["cell_updates"] == 0
     # a queued request that is cancelled never runs
     srv2 = P.Server(16 << 30, max_active=1, chunk_nodes=2, autotune=False)
     ids = [srv2.submit(full_req), srv2.submit(full_req)]
