@@ -453,6 +453,10 @@ int oed_server_checkpoint(oed_server *srv, unsigned long long id, double *H, int
 /* The JSON metrics line of finished request id, NUL-terminated, into buf[cap];
  * OED_PENDING if it has not finished, OED_ENOMEM if cap is too small. */
 int oed_server_metrics(oed_server *srv, unsigned long long id, char *buf, size_t cap);
+/* Drop the record of finished request id (its result, per-node checkpoint and metrics
+ * line), which the server otherwise keeps until it is destroyed; the id is unknown
+ * afterwards.  OED_PENDING if the request has not finished, OED_EINVAL if unknown. */
+int oed_server_release(oed_server *srv, unsigned long long id);
 /* Device bytes reserved (running requests and idle workspaces), running and queued
  * request counts. */
 int oed_server_stats(oed_server *srv, size_t *in_use, int *active, int *queued);

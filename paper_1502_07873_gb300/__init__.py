@@ -35,7 +35,7 @@ SYMBOLS = ("oed_create", "oed_workspace_bytes", "oed_destroy", "oed_last_error",
            "oed_server_destroy", "oed_eig_subset", "oed_dlmc", "oed_hessian_ii", "oed_newton_step",
            "oed_hessian_map", "oed_wait_selftest", "oed_rebind", "oed_server_set_admission",
            "oed_server_set_log", "oed_server_cancel", "oed_server_checkpoint", "oed_server_metrics",
-           "oed_server_pool")
+           "oed_server_pool", "oed_server_release")
 
 
 class OedError(RuntimeError):
@@ -124,6 +124,7 @@ def library():
         "oed_server_checkpoint": (i, [vp, ctypes.c_ulonglong, dp, i, ip]),
         "oed_server_metrics": (i, [vp, ctypes.c_ulonglong, ctypes.c_char_p, sz]),
         "oed_server_pool": (i, [vp, ip, ctypes.POINTER(sz)]),
+        "oed_server_release": (i, [vp, ctypes.c_ulonglong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -554,6 +555,11 @@ class Server:
                                                      H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                      H.shape[0], ctypes.byref(k)), "oed_server_checkpoint")
         return H[:k.value]
+
+    def release(self, rid: int) -> int:
+        """Drop a finished request's record; returns the status code (OED_PENDING if it is
+        still running)."""
+        return int(library().oed_server_release(self.handle, rid))
 
     def metrics(self, rid: int) -> dict:
         """The finished request's JSON metrics line, parsed."""

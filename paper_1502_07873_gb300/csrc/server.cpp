@@ -583,6 +583,17 @@ int oed_server_metrics(oed_server *srv, unsigned long long id, char *buf, size_t
     return OED_OK;
 }
 
+int oed_server_release(oed_server *srv, unsigned long long id)
+{
+    if (!srv) return OED_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->results.find(id);
+    if (it == srv->results.end()) return OED_EINVAL;
+    if (!it->second.done) return OED_PENDING;
+    srv->results.erase(it);
+    return OED_OK;
+}
+
 int oed_server_stats(oed_server *srv, size_t *in_use, int *active, int *queued)
 {
     if (!srv) return OED_EINVAL;

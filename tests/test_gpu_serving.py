@@ -264,6 +264,11 @@ def test_metrics_lines(P, tmp_path):
                                      w.prior_lo, w.prior_hi, w.rel_step, 0.05, 1, tag=100 + s))
            for s in range(3)]
     res = [srv.wait(i) for i in ids]
+    # a finished request's record can be dropped; its id is unknown afterwards
+    assert srv.release(ids[0]) == P.OED_OK
+    assert srv.release(ids[0]) == P.OED_EINVAL
+    with pytest.raises(P.OedError):
+        srv.poll(ids[0])
     srv.close()
     lines = [json.loads(x) for x in log.read_text().splitlines()]
     assert sorted(d["tag"] for d in lines) == [100, 101, 102]
