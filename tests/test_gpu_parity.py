@@ -512,3 +512,42 @@ def test_resident_one_row_per_cta(P, oracle):
     for k in range(2):
         ref = oracle.forward(G, th[k])
         assert _normwise(g[k].cpu().numpy(), ref) <= 1e-4
+
+
+def test_rebind_matches_a_fresh_context(P):
+    """oed_rebind re-targets a context's workspace at a problem of the same grid shape with
+    another step count, medium and receivers: seismograms and Hessians equal a fresh
+    context's bit for bit; another shape is refused (OED_EINVAL), a problem whose workspace
+    does not fit is refused (OED_ENOMEM) and the context still works."""
+    w1 = W.tiny(nx=81, nz=41, h=25.0, nsteps=120, nrec=5)
+    w2 = W.tiny(nx=81, nz=41, h=25.0, nsteps=90, nrec=3, layers=W.THREE_LAYER)
+    th = np.array([[1000.0, 480.0, 0.12, 6.0, 5e13, 2e13, 7e13], [950.0, 520.0, 0.2, 5.0, 3e13, 6e13, 2e13]])
+    for prec in (P.OED_FP32, P.OED_FP64):
+        ctx = P.Context(P.problem_from_workload(w1, prec), max_solves=30)
+        g1 = torch.empty((2, w1.nlevels, w1.nrec, 2), dtype=torch.float64, device=DEV)
+        P.oed_forward(ctx, _t(th), g1)
+        ctx.rebind(P.problem_from_workload(w2, prec))
+        g2 = torch.empty((2, w2.nlevels, w2.nrec, 2), dtype=torch.float64, device=DEV)
+        P.oed_forward(ctx, _t(th), g2)
+        H2 = torch.empty((2, 7, 7), dtype=torch.float64, device=DEV)
+        P.oed_hessian(ctx, _t(th), w2.prior_lo, w2.prior_hi, w2.rel_step, 0.05, H2)
+        fresh = P.Context(P.problem_from_workload(w2, prec), max_solves=30)
+        g2f = torch.empty_like(g2)
+        P.oed_forward(fresh, _t(th), g2f)
+        H2f = torch.empty_like(H2)
+        P.oed_hessian(fresh, _t(th), w2.prior_lo, w2.prior_hi, w2.rel_step, 0.05, H2f)
+        torch.cuda.synchronize()
+        assert torch.equal(g2, g2f) and torch.equal(H2, H2f)
+        with pytest.raises(P.OedError) as e:
+            ctx.rebind(P.problem_from_workload(W.tiny(nx=61, nz=41, h=25.0, nsteps=90, nrec=3), prec))
+        assert e.value.code == P.OED_EINVAL
+        with pytest.raises(P.OedError) as e:   # a longer record needs a larger workspace
+            ctx.rebind(P.problem_from_workload(W.tiny(nx=81, nz=41, h=25.0, nsteps=4000, nrec=5), prec))
+        assert e.value.code == P.OED_ENOMEM
+        ctx.rebind(P.problem_from_workload(w1, prec))
+        g1b = torch.empty_like(g1)
+        P.oed_forward(ctx, _t(th), g1b)
+        torch.cuda.synchronize()
+        assert torch.equal(g1, g1b)
+        fresh.close()
+        ctx.close()
