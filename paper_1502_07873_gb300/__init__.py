@@ -156,6 +156,31 @@ def _ptr(t) -> Optional[int]:
     return t.data_ptr()
 
 
+def _arg(t, name: str, dtype: str, numel: int = 0, rows: Optional[int] = None):
+    """Device pointer of a tensor argument, after checking what the C call will read or
+    write through it (a wrong dtype or a short tensor would be accessed past its end on
+    the device): its dtype ("f64", "i32" or "u8"), at least `numel` elements, `rows` rows
+    of 7 when given (a parameter array), then that it is a contiguous CUDA tensor."""
+    if t is None:
+        return None
+    import torch
+    want = {"f64": torch.float64, "i32": torch.int32, "u8": torch.uint8}[dtype]
+    if t.dtype != want:
+        raise ValueError(f"{name}: expected {want}, got {t.dtype}")
+    if rows is not None and (t.dim() != 2 or t.shape[0] != rows or t.shape[1] != NTHETA):
+        raise ValueError(f"{name}: expected shape [{rows}][7], got {list(t.shape)}")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: needs at least {numel} elements, has {t.numel()}")
+    return _ptr(t)
+
+
+def _theta(theta, name: str = "theta"):
+    """Node count of a parameter array theta[n][7] (FP64), checked."""
+    if theta.dim() != 2 or theta.shape[1] != NTHETA:
+        raise ValueError(f"{name}: expected shape [n][7], got {list(theta.shape)}")
+    return int(theta.shape[0])
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -280,8 +305,9 @@ class Context:
 
 def oed_forward(ctx: Context, theta, g, stream=None):
     """Seismograms g[n][nsteps+1][nrec][2] (FP64, device) of theta[n][7] (FP64, device)."""
-    n = theta.shape[0]
-    _check(ctx.handle, library().oed_forward(ctx.handle, _ptr(theta), n, _ptr(g), _stream(stream)),
+    n = _theta(theta)
+    _check(ctx.handle, library().oed_forward(ctx.handle, _arg(theta, "theta", "f64", rows=n), n,
+                                             _arg(g, "g", "f64", n * ctx.nlev * ctx.nrec * 2), _stream(stream)),
            "oed_forward")
     return g
 
@@ -290,12 +316,13 @@ def oed_hessian(ctx: Context, theta, lo: Sequence[float], hi: Sequence[float], r
                 sigma: float, H, win_levels: Optional[Sequence[int]] = None, H_rec=None,
                 status=None, stream=None):
     """Gauss-Newton Hessians H[n][7][7] (device) from central-FD solves."""
-    n = theta.shape[0]
+    n = _theta(theta)
     nwin = 0 if win_levels is None else len(win_levels)
     wl = (ctypes.c_int * max(1, nwin))(*(win_levels or [0]))
-    rc = library().oed_hessian(ctx.handle, _ptr(theta), n, _darr(lo), _darr(hi), float(rel_step),
-                               float(sigma), wl if nwin else None, nwin, _ptr(H), _ptr(H_rec),
-                               _ptr(status), _stream(stream))
+    rc = library().oed_hessian(ctx.handle, _arg(theta, "theta", "f64", rows=n), n, _darr(lo), _darr(hi),
+                               float(rel_step), float(sigma), wl if nwin else None, nwin,
+                               _arg(H, "H", "f64", n * 49), _arg(H_rec, "H_rec", "f64", n * ctx.nrec * nwin * 28),
+                               _arg(status, "status", "i32", n), _stream(stream))
     _check(ctx.handle, rc, "oed_hessian")
     return H
 
@@ -305,8 +332,9 @@ def oed_eig(ctx: Optional[Context], H, w, lo, hi, eig, dkl=None, status=None, n_
     """EIG = sum_i w_i D_KL-hat(H_i) into eig[1] (device)."""
     n = H.shape[0]
     h = ctx.handle if ctx is not None else None
-    rc = library().oed_eig(h, _ptr(H), n, _ptr(w), _darr(lo), _darr(hi), _ptr(eig), _ptr(dkl),
-                           _ptr(status), _ptr(n_bad), _stream(stream))
+    rc = library().oed_eig(h, _arg(H, "H", "f64", n * 49), n, _arg(w, "w", "f64", n), _darr(lo), _darr(hi),
+                           _arg(eig, "eig", "f64", 1), _arg(dkl, "dkl", "f64", n), _arg(status, "status", "i32", n),
+                           _arg(n_bad, "n_bad", "i32", 1), _stream(stream))
     _check(h, rc, "oed_eig")
     return eig
 
@@ -320,8 +348,10 @@ def oed_eig_subset(ctx: Optional[Context], H, w, lo, hi, free, eig, dkl=None, st
         mask |= 1 << int(j)
     n = H.shape[0]
     h = ctx.handle if ctx is not None else None
-    rc = library().oed_eig_subset(h, _ptr(H), n, _ptr(w), _darr(lo), _darr(hi), mask, _ptr(eig),
-                                  _ptr(dkl), _ptr(status), _ptr(n_bad), _stream(stream))
+    rc = library().oed_eig_subset(h, _arg(H, "H", "f64", n * 49), n, _arg(w, "w", "f64", n), _darr(lo),
+                                  _darr(hi), mask, _arg(eig, "eig", "f64", 1), _arg(dkl, "dkl", "f64", n),
+                                  _arg(status, "status", "i32", n), _arg(n_bad, "n_bad", "i32", 1),
+                                  _stream(stream))
     _check(h, rc, "oed_eig_subset")
     return eig
 
@@ -333,9 +363,11 @@ def oed_wait_selftest(ctx: Context, seconds: float = 0.05, stream=None) -> int:
 
 def oed_hessian_ii(ctx: Context, theta, y, sigma: float, H, grad=None, status=None, stream=None):
     """Adds H_II (Alg. 1 steps 6-10) at theta for data y to H; dL/dtheta into grad."""
-    n = theta.shape[0]
-    _check(ctx.handle, library().oed_hessian_ii(ctx.handle, _ptr(theta), n, _ptr(y), float(sigma), _ptr(H),
-                                                _ptr(grad), _ptr(status), _stream(stream)), "oed_hessian_ii")
+    n = _theta(theta)
+    _check(ctx.handle, library().oed_hessian_ii(ctx.handle, _arg(theta, "theta", "f64", rows=n), n,
+                                                _arg(y, "y", "f64", n * ctx.nlev * ctx.nrec * 2), float(sigma),
+                                                _arg(H, "H", "f64", n * 49), _arg(grad, "grad", "f64", n * 7),
+                                                _arg(status, "status", "i32", n), _stream(stream)), "oed_hessian_ii")
     return H
 
 
@@ -348,8 +380,10 @@ def _mask(free):
 
 def oed_newton_step(H, grad, theta, lo, hi, free=range(7), status=None, stream=None):
     """theta_F += -H_FF^-1 grad_F per node over the unknowns F, clamped to [lo, hi]."""
-    _check(None, library().oed_newton_step(_ptr(H), _ptr(grad), theta.shape[0], _darr(lo), _darr(hi), _mask(free),
-                                           _ptr(theta), _ptr(status), _stream(stream)), "oed_newton_step")
+    n = _theta(theta)
+    _check(None, library().oed_newton_step(_arg(H, "H", "f64", n * 49), _arg(grad, "grad", "f64", n * 7), n,
+                                           _darr(lo), _darr(hi), _mask(free), _arg(theta, "theta", "f64", rows=n),
+                                           _arg(status, "status", "i32", n), _stream(stream)), "oed_newton_step")
     return theta
 
 
@@ -357,9 +391,12 @@ def oed_hessian_map(ctx: Context, theta, y, lo, hi, rel_step: float, sigma: floa
                     free=range(7), status=None, stream=None):
     """Newton iterations over the unknowns F to the estimate of Thm 1; H = H_1 + H_II and
     grad at it."""
-    _check(ctx.handle, library().oed_hessian_map(ctx.handle, _ptr(theta), theta.shape[0], _ptr(y), _darr(lo),
+    n = _theta(theta)
+    _check(ctx.handle, library().oed_hessian_map(ctx.handle, _arg(theta, "theta", "f64", rows=n), n,
+                                                 _arg(y, "y", "f64", n * ctx.nlev * ctx.nrec * 2), _darr(lo),
                                                  _darr(hi), float(rel_step), float(sigma), _mask(free), int(iters),
-                                                 _ptr(H), _ptr(grad), _ptr(status), _stream(stream)),
+                                                 _arg(H, "H", "f64", n * 49), _arg(grad, "grad", "f64", n * 7),
+                                                 _arg(status, "status", "i32", n), _stream(stream)),
            "oed_hessian_map")
     return H
 
@@ -372,8 +409,10 @@ def oed_dlmc(g_outer, eps, g_inner, sigma, log_ev, eig=None, stream=None):
     D = g_outer[0].numel()
     if g_inner[0].numel() != D or eps.shape[0] != N:
         raise ValueError("oed_dlmc: shapes")
-    _check(None, library().oed_dlmc(_ptr(g_outer), _ptr(eps), N, _ptr(g_inner), M, D, float(sigma),
-                                    _ptr(log_ev), _ptr(eig), _stream(stream)), "oed_dlmc")
+    _check(None, library().oed_dlmc(_arg(g_outer, "g_outer", "f64", N * D), _arg(eps, "eps", "f64", N * D), N,
+                                    _arg(g_inner, "g_inner", "f64", M * D), M, D, float(sigma),
+                                    _arg(log_ev, "log_ev", "f64", N), _arg(eig, "eig", "f64", 1), _stream(stream)),
+           "oed_dlmc")
     return eig
 
 
@@ -382,16 +421,21 @@ def oed_eig_designs(ctx: Optional[Context], H_rec, win: int, mask, w, lo, hi, ei
     """EIG of every receiver design in mask[ndesign][nrec] from H_rec[n][nrec][nwin][28]."""
     n, nrec, nwin = H_rec.shape[0], H_rec.shape[1], H_rec.shape[2]
     h = ctx.handle if ctx is not None else None
-    rc = library().oed_eig_designs(h, _ptr(H_rec), n, nrec, nwin, int(win), _ptr(mask),
-                                   mask.shape[0], _ptr(w), _darr(lo), _darr(hi), _ptr(eig),
-                                   _ptr(n_bad), _stream(stream))
+    nd = mask.shape[0]
+    if mask.dim() != 2 or mask.shape[1] != nrec:
+        raise ValueError(f"mask: expected shape [ndesign][{nrec}], got {list(mask.shape)}")
+    rc = library().oed_eig_designs(h, _arg(H_rec, "H_rec", "f64", n * nrec * nwin * 28), n, nrec, nwin, int(win),
+                                   _arg(mask, "mask", "u8", nd * nrec), nd, _arg(w, "w", "f64", n), _darr(lo),
+                                   _darr(hi), _arg(eig, "eig", "f64", nd), _arg(n_bad, "n_bad", "i32", nd),
+                                   _stream(stream))
     _check(h, rc, "oed_eig_designs")
     return eig
 
 
 def oed_nodes_mc(u, lo, hi, theta, w, stream=None):
-    rc = library().oed_nodes_mc(_ptr(u), u.shape[0], _darr(lo), _darr(hi), _ptr(theta), _ptr(w),
-                                _stream(stream))
+    M = _theta(u, "u")
+    rc = library().oed_nodes_mc(_arg(u, "u", "f64", rows=M), M, _darr(lo), _darr(hi),
+                                _arg(theta, "theta", "f64", rows=M), _arg(w, "w", "f64", M), _stream(stream))
     _check(None, rc, "oed_nodes_mc")
     return theta, w
 

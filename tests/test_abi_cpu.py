@@ -235,3 +235,36 @@ def test_spread_sample_takes_both_ends_of_each_interval():
     for j in range(4):
         assert int(np.argmin(u[:, j])) in idx or np.argmin(u[:, j]) in (0, 1)
         assert int(np.argmax(u[:, j])) in idx or np.argmax(u[:, j]) in (0, 1)
+
+
+def test_binding_checks_tensor_arguments_before_the_device(P):
+    """The binding refuses a tensor of the wrong dtype, too few elements or the wrong
+    parameter shape before anything reaches the library (such a tensor would be read or
+    written past its end on the device); these calls need no context."""
+    torch = pytest.importorskip("torch")
+    lo, hi = W.PRIOR_LO, W.PRIOR_HI
+    H = torch.zeros((2, 7, 7), dtype=torch.float64)
+    w = torch.zeros(2, dtype=torch.float64)
+    eig = torch.zeros(1, dtype=torch.float64)
+    # each defect sits in the first tensor the call checks (the checks run argument by
+    # argument; on a GPU every argument is a device tensor and all are checked)
+    cases = [
+        (lambda: P.oed_eig(None, H.float(), w, lo, hi, eig), "H: expected torch.float64"),
+        (lambda: P.oed_eig(None, torch.zeros((2, 7, 6), dtype=torch.float64), w, lo, hi, eig),
+         "H: needs at least 98"),
+        (lambda: P.oed_nodes_mc(torch.zeros((3, 6), dtype=torch.float64), lo, hi,
+                                torch.zeros((3, 7), dtype=torch.float64), torch.zeros(3, dtype=torch.float64)),
+         "u: expected shape"),
+        (lambda: P.oed_newton_step(H, torch.zeros((2, 7), dtype=torch.float64),
+                                   torch.zeros((2, 6), dtype=torch.float64), lo, hi), "theta: expected shape"),
+        (lambda: P.oed_dlmc(torch.zeros((4, 5), dtype=torch.float64), torch.zeros((3, 5), dtype=torch.float64),
+                            torch.zeros((3, 5), dtype=torch.float64), 0.1, torch.zeros(4, dtype=torch.float64)),
+         "shapes"),
+        (lambda: P.oed_eig_designs(None, torch.zeros((2, 4, 1, 28), dtype=torch.float64), 0,
+                                   torch.zeros((3, 5), dtype=torch.uint8), w, lo, hi, eig), "mask: expected shape"),
+        # well-formed, but host tensors: refused as well, since the calls take device memory
+        (lambda: P.oed_eig(None, H, w, lo, hi, eig), "expected a CUDA tensor"),
+    ]
+    for call, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            call()
