@@ -255,7 +255,8 @@ class Context:
 
     def rebind(self, problem: Problem):
         """Re-target this context's workspace at another problem of the same grid shape and
-        precision (oed_rebind)."""
+        precision (oed_rebind).  The streams of earlier calls on this context must be
+        synchronised first (the new problem's tables are written on the context's own stream)."""
         _check(self.handle, library().oed_rebind(self.handle, ctypes.byref(problem)), "oed_rebind")
         self.problem = problem
         self.nrec = problem.nrec

@@ -526,6 +526,8 @@ def test_rebind_matches_a_fresh_context(P):
         ctx = P.Context(P.problem_from_workload(w1, prec), max_solves=30)
         g1 = torch.empty((2, w1.nlevels, w1.nrec, 2), dtype=torch.float64, device=DEV)
         P.oed_forward(ctx, _t(th), g1)
+        torch.cuda.synchronize()   # oed_rebind wants the context's earlier work finished
+        assert not torch.isnan(g1).any(), prec
         ctx.rebind(P.problem_from_workload(w2, prec))
         g2 = torch.empty((2, w2.nlevels, w2.nrec, 2), dtype=torch.float64, device=DEV)
         P.oed_forward(ctx, _t(th), g2)
