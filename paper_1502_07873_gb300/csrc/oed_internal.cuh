@@ -46,8 +46,8 @@ struct __align__(16 * sizeof(real)) RowCoef {
 
 // The same update regrouped so that FP32 rounds as little as possible at the
 // scale of u itself: every neighbour enters through a difference, the operator
-// term is summed at the (small) scale of those differences, and u^{m+1} is formed
-// as u^m + ((u^m - u^{m-1}) + A), one rounding at the scale of u per step.
+// term is summed at the (small) scale of those differences, onto u^m - u^{m-1},
+// and u^{m+1} is formed as u^m + that sum: one rounding at the scale of u per step.
 //   A_x = axx lap_x + axzp dv_s + naxzm dv_n + px dz_s + nqx dz_n
 //   A_z = azx lap_z + azzp dw_s + nazzm dw_n + pz dx_s + nqz dx_n
 // with lap_x = (x_e - x_c) - (x_c - x_w), dv_s = x_s - x_c, dv_n = x_c - x_n (dw for

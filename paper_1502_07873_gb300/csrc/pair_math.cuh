@@ -41,8 +41,25 @@ __device__ __forceinline__ bool kp_equal(const KP &a, const KP &b)
 
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-// a - b as one rounding: b * (-1) is exact, so fma(b, -1, a) rounds a - b once
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// a - b, rounded once per component, in two forms with the same bits: fma(b, -1, a) (the
+// product b * -1 is exact) and the packed subtract sub.rn.f32x2.  The cluster-resident
+// kernel runs faster with the second (PS), the two-step TMA kernel with the first.
+template <bool PS>
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    if constexpr (PS) {
+        float2 d;
+        asm("{\n\t.reg .b64 x, y, z;\n\t"
+            "mov.b64 x, {%2, %3};\n\t"
+            "mov.b64 y, {%4, %5};\n\t"
+            "sub.rn.f32x2 z, x, y;\n\t"
+            "mov.b64 {%0, %1}, z;\n\t}"
+            : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+        return d;
+    } else {
+        return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+    }
+}
 
 // Row2 with each quantity as a (x, z) pair per column a = c, b = c+1; the east - west
 // differences, which enter the other component's update, are stored swapped (z, x)
@@ -53,39 +70,42 @@ struct Row2P {
     float2 va, vb;   // south row minus this row
 };
 
+template <bool PS = false>
 __device__ __forceinline__ void row_fromP(float2 w, float4 m, float2 e, Row2P &r)
 {
     r.ca = make_float2(m.x, m.y);
     r.cb = make_float2(m.z, m.w);
-    const float2 t = sub2(r.cb, r.ca);
-    r.la = sub2(t, sub2(r.ca, w));
-    r.lb = sub2(sub2(e, r.cb), t);
+    const float2 t = sub2<PS>(r.cb, r.ca);
+    r.la = sub2<PS>(t, sub2<PS>(r.ca, w));
+    r.lb = sub2<PS>(sub2<PS>(e, r.cb), t);
     r.da = make_float2(m.w - w.y, m.z - w.x);
     r.db = make_float2(e.y - m.y, e.x - m.x);
 }
 
+template <bool PS = false>
 __device__ __forceinline__ void southP(Row2P &c, const Row2P &s)
 {
-    c.va = sub2(s.ca, c.ca);
-    c.vb = sub2(s.cb, c.cb);
+    c.va = sub2<PS>(s.ca, c.ca);
+    c.vb = sub2<PS>(s.cb, c.cb);
 }
 
 // u^{m+1} of the pair (u holds u^{m-1} on entry, slot order x_a, z_a, x_b, z_b)
+template <bool PS = false>
 __device__ __forceinline__ void pair_updateP(const KP &K, const Row2P &n, const Row2P &c, const Row2P &s,
                                              float4 &u)
 {
-    float2 A = __fmul2_rn(K.a, c.la);
+    float2 A = fma2(K.a, c.la, sub2<PS>(c.ca, make_float2(u.x, u.y)));
     A = fma2(K.vs, c.va, A);
     A = fma2(K.vn, n.va, A);
     A = fma2(K.ds, s.da, A);
     A = fma2(K.dn, n.da, A);
-    float2 B = __fmul2_rn(K.a, c.lb);
+    float2 B = fma2(K.a, c.lb, sub2<PS>(c.cb, make_float2(u.z, u.w)));
     B = fma2(K.vs, c.vb, B);
     B = fma2(K.vn, n.vb, B);
     B = fma2(K.ds, s.db, B);
     B = fma2(K.dn, n.db, B);
-    const float2 xa = add2(c.ca, add2(sub2(c.ca, make_float2(u.x, u.y)), A));
-    const float2 xb = add2(c.cb, add2(sub2(c.cb, make_float2(u.z, u.w)), B));
+    const float2 xa = add2(c.ca, A);
+    const float2 xb = add2(c.cb, B);
     u = make_float4(xa.x, xa.y, xb.x, xb.y);
 }
 

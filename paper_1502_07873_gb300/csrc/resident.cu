@@ -27,9 +27,10 @@
 // The surface row, the bottom row and the rows whose neighbour lives in another
 // CTA are peeled off the main loop, and so are the march's last one to three rows
 // (the only ones that do not prefetch): the unrolled march body has no branch.  The
-// absorbing side columns are patched by the threads that own them, in a second
-// compiled march that only the warps holding a side column run; the source term
-// is added after the sweep to the few patch nodes.  The arithmetic runs on packed
+// absorbing side columns are left out of the march (its stores to them are
+// predicated off) and written by a separate edge warp from u^m alone, so the warps
+// that hold a side column march exactly like the others; the source term is added
+// after the sweep to the few patch nodes.  The arithmetic runs on packed
 // (x, z) pairs (.f32x2).  HBM traffic is only the seismogram samples and the source
 // time function: the wavefield never leaves the chip, so this kernel is bound by
 // shared-memory latency and throughput and the per-step barrier, not by HBM.
@@ -41,10 +42,12 @@ namespace oed {
 
 // Block size and register cap: registers are split over the SM's four schedulers
 // (16 K each), so 20 warps of 96 registers is the most one CTA can hold (the packed
-// update needs 80).  Three row segments of about twelve rows per column pair (19
-// warps at 401 columns) measured faster than one, two, four or five.
+// update needs about 90).  The last warp is the edge warp; three row segments of about
+// twelve rows per column pair (19 march warps at 401 columns) measured faster than one,
+// two, four or five.
 constexpr int kResThreads = 640;
 constexpr int kResRegs = 96;
+constexpr bool kPS = true;   // the packed-subtract form of the pair arithmetic
 
 struct ResArgs {
     const FacCoef<float> *fac;     // [nz]
@@ -58,6 +61,7 @@ struct ResArgs {
     int npair;                     // column pairs per row, (nx + 1) / 2
     int nseg;                      // row segments per column pair
     int rps;                       // rows per segment
+    int nmarch;                    // threads of the march warps; the last warp is the edge warp
 };
 
 __device__ __forceinline__ unsigned cluster_rank()
@@ -104,15 +108,26 @@ __device__ __forceinline__ float4 pair_at(const float2 *q, int sq)
     return make_float4(e.x, e.y, o.x, o.y);
 }
 
-__device__ __forceinline__ void pair_put(float2 *q, int sq, float4 u)
+// The pair's slots in the level being written (u^{m-1} in, u^{m+1} out), at per-thread
+// offsets offE (column c) and offO (column c + 1) from q: 0 and sq for interior pairs.  A
+// side column (or the ghost column nx) is written by the edge warp, not by the march, so
+// its thread's slot is moved to a ghost slot that no thread reads (even slot 0, or slot
+// npair + 1 of either half): the march's stores stay unconditional.
+__device__ __forceinline__ float4 pair_at_n(const float2 *q, int offE, int offO)
 {
-    q[0] = make_float2(u.x, u.y);
-    q[sq] = make_float2(u.z, u.w);
+    const float2 e = q[offE], o = q[offO];
+    return make_float4(e.x, e.y, o.x, o.y);
+}
+
+__device__ __forceinline__ void pair_put_n(float2 *q, int offE, int offO, float4 u)
+{
+    q[offE] = make_float2(u.x, u.y);
+    q[offO] = make_float2(u.z, u.w);
 }
 
 __device__ __forceinline__ void load_row(const float2 *q, int sq, Row2P &r)
 {
-    row_fromP(q[sq - 1], pair_at(q, sq), q[1], r);
+    row_fromP<kPS>(q[sq - 1], pair_at(q, sq), q[1], r);
 }
 
 // the same slots of a row in CTA `nb` of the cluster
@@ -127,7 +142,7 @@ __device__ __forceinline__ void load_row_remote(const float2 *q, int sq, unsigne
 {
     const unsigned b = remote_addr(smem_addr(q), nb);
     const float2 e = ld_cluster2(b), o = ld_cluster2(b + 8u * (unsigned)sq);
-    row_fromP(ld_cluster2(b + 8u * (unsigned)(sq - 1)), make_float4(e.x, e.y, o.x, o.y), ld_cluster2(b + 8u), r);
+    row_fromP<kPS>(ld_cluster2(b + 8u * (unsigned)(sq - 1)), make_float4(e.x, e.y, o.x, o.y), ld_cluster2(b + 8u), r);
 }
 
 // float offset of node (column i, component comp) within a shared row
@@ -158,25 +173,36 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     for (int k = tid; k < 2 * kPatch * kPatch; k += nthr)
         sw[k] = k < kPatch * kPatch ? a.src[blockIdx.y].wx[k] : a.src[blockIdx.y].wz[k - kPatch * kPatch];
 
-    // threads are packed densely over (segment, pair): a warp may straddle two segments
+    // march threads are packed densely over (segment, pair): a warp may straddle two
+    // segments.  The last warp (the edge warp) takes the absorbing side columns, which
+    // the march does not store, and the receiver samples: side columns read only u^m, so
+    // this needs no synchronisation with the march, and no march warp is slowed down by
+    // the absorbing patch of a side column.
+    const bool edge = tid >= a.nmarch;
     const int p = tid % a.npair;
     const int c = 2 * p;
     const int seg = tid / a.npair;
-    const bool active = seg < a.nseg;
+    const bool active = !edge && seg < a.nseg;
     const int kind = (c == 0 ? 1 : 0) | (c + 1 == g.nx - 1 ? 2 : 0) | (c == g.nx - 1 ? 4 : 0);
+    const int offE = (kind & 1) ? -1 : ((kind & 4) ? 1 : 0);
+    const int offO = a.sq + ((kind & 6) ? 1 : 0);
     const int l0 = seg * a.rps;
     const int l1 = min(l0 + a.rps, nrows);
     const bool top = (j0 + l0 == 0);
     const SourceDesc<float> *sd = a.src + s;
-    const int sj = sd->j0;
+    const int sj = sd->j0, si0 = sd->i0;
     const int siA = c - sd->i0, siB = c + 1 - sd->i0;
     const bool scolA = (unsigned)siA < (unsigned)kPatch;
     const bool scolB = c + 1 < g.nx && (unsigned)siB < (unsigned)kPatch;
     const float *stf = a.stf + (size_t)s * g.nsteps;
+    // The source term of the patch nodes is added by the edge warp once the march warps
+    // that own patch nodes of this CTA have stored them: those warps arrive at named
+    // barrier 1 after their march (without waiting), the edge warp waits there.  The
+    // count is fixed per CTA, so every step's barrier completes.
+    const int srow0 = max(sj, j0), srow1 = min(sj + kPatch, j0 + nrows);   // patch rows in this CTA
+    const bool patch = active && (scolA || scolB) && sj + kPatch > j0 + l0 && sj < j0 + l1;
+    const bool patch_warp = __any_sync(0xffffffffu, patch);
     float *trace = a.trace + (size_t)s * g.nlev * g.nrec * 2;
-    // the warps that hold a side column run the march with the absorbing patch, the
-    // others (most of them) a march without it
-    const bool warp_side = __any_sync(0xffffffffu, active && kind != 0);
     // when every row the march visits in this CTA (rows 1 or 0 .. nrows-2: the surface and
     // the last row are peeled) has the coefficients of the first, as in a homogeneous
     // medium, the march keeps them in registers instead of reloading them row by row
@@ -186,15 +212,32 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
     for (int k = kfirst + 1 + tid; k < nrows - 1; k += nthr) same &= kp_equal(coef[k], coef[kfirst]);
     const bool unif = __syncthreads_and(same) != 0 && kfirst < nrows - 1;
     const KP K0 = coef[min(kfirst, nrows - 1)];
+    const int npw = __syncthreads_count(patch_warp && (tid & 31) == 0);
     cluster_barrier();
 
     for (int m = 0; m < g.nsteps; m++) {
         const float2 *cur = ((m & 1) ? B : A) + p + 1;   // this thread's even slot in row 0
         float2 *nxt = ((m & 1) ? A : B) + p + 1;
-        if (rank == 0) {
-            const float *row0 = reinterpret_cast<const float *>((m & 1) ? B : A);
-            for (int q = tid; q < 2 * g.nrec; q += nthr)
-                trace[(size_t)m * g.nrec * 2 + q] = row0[node_off(a.rec[q >> 1], q & 1, sq)];
+        if (edge) {
+            const int e = tid - a.nmarch;
+            const float *cf = reinterpret_cast<const float *>((m & 1) ? B : A);   // u^m
+            float *nf = reinterpret_cast<float *>((m & 1) ? A : B);               // u^{m+1}
+            if (rank == 0)
+                for (int q = e; q < 2 * g.nrec; q += 32)
+                    trace[(size_t)m * g.nrec * 2 + q] = cf[node_off(a.rec[q >> 1], q & 1, sq)];
+            // side columns 0 and nx-1 (first-order absorbing, from the inward neighbour;
+            // they take precedence at the surface and bottom corners)
+            const int oL = node_off(0, 0, sq), oL1 = node_off(1, 0, sq);
+            const int oR = node_off(g.nx - 1, 0, sq), oR1 = node_off(g.nx - 2, 0, sq);
+            for (int l = e; l < nrows; l += 32) {
+                const float2 cpcs = coef[l].c;
+                const float *cr = cf + (size_t)l * RS * 2;
+                float *nr = nf + (size_t)l * RS * 2;
+                nr[oL] = absorb(cr[oL], cr[oL1], cpcs.x);
+                nr[oL + 1] = absorb(cr[oL + 1], cr[oL1 + 1], cpcs.y);
+                nr[oR] = absorb(cr[oR], cr[oR1], cpcs.x);
+                nr[oR + 1] = absorb(cr[oR + 1], cr[oR1 + 1], cpcs.y);
+            }
         }
         if (active && l0 < l1) {
             Row2P rn, rc, rs;
@@ -205,15 +248,14 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                     load_row(cur + (l + 1) * RS, sq, rs);
                 else   // a one-row slab
                     load_row_remote(cur, sq, rank + 1, rs);
-                southP(rc, rs);
+                southP<kPS>(rc, rs);
                 Row2P nt = rc;
                 nt.va = nt.vb = make_float2(0.0f, 0.0f);
                 float2 *o = nxt + l * RS;
-                float4 u = pair_at(o, sq);
+                float4 u = pair_at_n(o, offE, offO);
                 const KP K = coef[l];
-                pair_updateP(K, nt, rc, rs, u);
-                if (kind) absorbingP(K.c, u, rc, false, kind, u);
-                pair_put(o, sq, u);
+                pair_updateP<kPS>(K, nt, rc, rs, u);
+                pair_put_n(o, offE, offO, u);
                 rn = rc;
                 rc = rs;
                 l++;
@@ -222,7 +264,7 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                     load_row(cur + (l - 1) * RS, sq, rn);
                 else
                     load_row_remote(cur + (R - 1) * RS, sq, rank - 1, rn);
-                southP(rn, rc);
+                southP<kPS>(rn, rc);
             }
             // rows whose south neighbour is a local row and that are not the bottom row:
             // unrolled by three with the three window rows taking turns
@@ -232,30 +274,26 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                 const float2 *sp = cur + (l + 1) * RS;
                 float2 *o = nxt + l * RS;
                 const KP *cf = coef + l;
-                float4 pm = pair_at(sp, sq), pu = pair_at(o, sq);
+                float4 pm = pair_at(sp, sq), pu = pair_at_n(o, offE, offO);
                 float2 pw = sp[sq - 1];
                 float2 pe = sp[1];
-                // side: the warp holds a side column (absorbing patch compiled in);
                 // pf: a row below the south row exists, prefetch it (every row but the last)
                 // unifK: the CTA's march rows share K0 (no coefficient loads)
-                auto march = [&](auto side, auto unifK) {
+                auto march = [&](auto unifK) {
                     auto row = [&](auto pf, const Row2P &wn, Row2P &wc, Row2P &ws) {
-                        row_fromP(pw, pm, pe, ws);
+                        row_fromP<kPS>(pw, pm, pe, ws);
                         float4 u = pu;
                         if constexpr (decltype(pf)::value) {
                             sp += RS;
                             pm = pair_at(sp, sq);
                             pw = sp[sq - 1];
                             pe = sp[1];
-                            pu = pair_at(o + RS, sq);
+                            pu = pair_at_n(o + RS, offE, offO);
                         }
-                        southP(wc, ws);
+                        southP<kPS>(wc, ws);
                         const KP K = decltype(unifK)::value ? K0 : *cf;
-                        pair_updateP(K, wn, wc, ws, u);
-                        if constexpr (decltype(side)::value) {
-                            if (kind) absorbingP(K.c, u, wc, false, kind, u);
-                        }
-                        pair_put(o, sq, u);
+                        pair_updateP<kPS>(K, wn, wc, ws, u);
+                        pair_put_n(o, offE, offO, u);
                         o += RS;
                         cf++;
                     };
@@ -286,60 +324,49 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
                     }
                     l = lstop;
                 };
-                // a warp-uniform choice: a branch inside the march body would split the
+                // a CTA-uniform choice: a branch inside the march body would split the
                 // unrolled rows into separate blocks and cost the scheduler its overlap
-                if (warp_side) {
-                    if (unif)
-                        march(std::true_type{}, std::true_type{});
-                    else
-                        march(std::true_type{}, std::false_type{});
-                } else {
-                    if (unif)
-                        march(std::false_type{}, std::true_type{});
-                    else
-                        march(std::false_type{}, std::false_type{});
-                }
+                if (unif)
+                    march(std::true_type{});
+                else
+                    march(std::false_type{});
             }
             // what is left: a last interior row whose south neighbour sits in CTA rank+1,
             // or the absorbing bottom row
             for (; l < l1; l++) {
                 const KP K = coef[l];
                 float2 *o = nxt + l * RS;
-                float4 u = pair_at(o, sq);
+                float4 u = pair_at_n(o, offE, offO);
                 if (j0 + l == g.nz - 1) {
                     const float4 nv = l > 0 ? pair_at(cur + (l - 1) * RS, sq)
                                             : pair_at_remote(cur + (R - 1) * RS, sq, rank - 1);
-                    absorbingP(K.c, nv, rc, true, kind, u);
+                    absorbingP(K.c, nv, rc, true, 0, u);
                 } else {
                     load_row_remote(cur, sq, rank + 1, rs);
-                    southP(rc, rs);
-                    pair_updateP(K, rn, rc, rs, u);
-                    if (kind) absorbingP(K.c, u, rc, false, kind, u);
+                    southP<kPS>(rc, rs);
+                    pair_updateP<kPS>(K, rn, rc, rs, u);
                 }
-                pair_put(o, sq, u);
+                pair_put_n(o, offE, offO, u);
                 rn = rc;
                 rc = rs;
             }
-            // source term: u^{m+1} += dt^2/nu f^m on the patch nodes this thread owns,
-            // added last as in the node update of the streaming kernel
-            if (scolA || scolB) {
-                const float S = stf[m];
-                float *nf = reinterpret_cast<float *>((m & 1) ? A : B);
-                for (int bb = 0; bb < kPatch; bb++) {
-                    const int lj = sj + bb - j0;
-                    if (lj < l0 || lj >= l1) continue;
-                    float *row = nf + (size_t)lj * RS * 2;
-                    if (scolA) {
-                        const int ia = node_off(c, 0, sq);
-                        row[ia] = add_force(row[ia], S, sw[bb * kPatch + siA]);
-                        row[ia + 1] = add_force(row[ia + 1], S, sw[kPatch * kPatch + bb * kPatch + siA]);
-                    }
-                    if (scolB) {
-                        const int ib = node_off(c + 1, 0, sq);
-                        row[ib] = add_force(row[ib], S, sw[bb * kPatch + siB]);
-                        row[ib + 1] = add_force(row[ib + 1], S, sw[kPatch * kPatch + bb * kPatch + siB]);
-                    }
-                }
+        }
+        if (patch_warp)
+            asm volatile("bar.arrive 1, %0;" :: "r"(32 * (npw + 1)) : "memory");
+        if (edge && npw > 0) {
+            // source term: u^{m+1} += dt^2/nu f^m on the patch nodes of this CTA, added last
+            // as in the node update of the streaming kernel (one node per lane)
+            asm volatile("bar.sync 1, %0;" :: "r"(32 * (npw + 1)) : "memory");
+            float *nf = reinterpret_cast<float *>((m & 1) ? A : B);
+            const float S = stf[m];
+            for (int k = tid - a.nmarch; k < kPatch * kPatch; k += 32) {
+                const int bb = k / kPatch, ai = k - bb * kPatch;
+                const int j = sj + bb;
+                if (j < srow0 || j >= srow1) continue;
+                float *row = nf + (size_t)(j - j0) * RS * 2;
+                const int o = node_off(si0 + ai, 0, sq);
+                row[o] = add_force(row[o], S, sw[k]);
+                row[o + 1] = add_force(row[o + 1], S, sw[kPatch * kPatch + k]);
             }
         }
         cluster_barrier();
@@ -354,7 +381,7 @@ __global__ void __maxnreg__(kResRegs) k_resident(ResArgs a)
 // Shape of the resident launch for a grid: cluster size C (1..8) and rows per CTA,
 // or C = 0 when the two levels do not fit in C CTAs of shared memory.
 struct ResShape {
-    int C, R, sq, npair, nseg, rps, threads;
+    int C, R, sq, npair, nseg, rps, nmarch, threads;
     size_t smem;
 };
 
@@ -362,14 +389,14 @@ static ResShape resident_shape(const Geometry &g, int C)
 {
     ResShape r{};
     const int npair = (g.nx + 1) / 2;
-    if (npair > kResThreads || C < 1 || C > 8) return r;
+    if (npair > kResThreads - 32 || C < 1 || C > 8) return r;
     const int R = (g.nz + C - 1) / C;
     if ((C - 1) * R >= g.nz) return r;   // a CTA would own no rows
     const int sq = npair + 2;   // ghost slots on both sides
     const size_t smem = (size_t)2 * R * sq * sizeof(float4) + (size_t)R * sizeof(KP) +
                         2 * kPatch * kPatch * sizeof(float);
     if (smem > 227 * 1024) return r;
-    int nseg = kResThreads / npair;
+    int nseg = (kResThreads - 32) / npair;   // the last warp is the edge warp
     if (nseg > R) nseg = R;
     r.C = C;
     r.R = R;
@@ -377,7 +404,8 @@ static ResShape resident_shape(const Geometry &g, int C)
     r.npair = npair;
     r.nseg = nseg;
     r.rps = (R + nseg - 1) / nseg;
-    r.threads = (npair * nseg + 31) / 32 * 32;
+    r.nmarch = (npair * nseg + 31) / 32 * 32;
+    r.threads = r.nmarch + 32;
     r.smem = smem;
     return r;
 }
@@ -451,6 +479,7 @@ cudaError_t launch_resident(const oed_ctx *ctx, int C, int nsolve, cudaStream_t 
     a.npair = r.npair;
     a.nseg = r.nseg;
     a.rps = r.rps;
+    a.nmarch = r.nmarch;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(r.C, nsolve, 1);
     cfg.blockDim = dim3(r.threads, 1, 1);

@@ -14,16 +14,15 @@ __device__ __forceinline__ double fma_(double a, double b, double c) { return fm
 __device__ __forceinline__ float add_force(float u, float S, float w) { return __fadd_rn(u, __fmul_rn(S, w)); }
 __device__ __forceinline__ double add_force(double u, double S, double w) { return __dadd_rn(u, __dmul_rn(S, w)); }
 
-__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
 
 // Operator term A_x of FacCoef (dt^2/nu times (A_h u)_x) from the differences
-// around the node: lap = (x_e - x_c) - (x_c - x_w), dvs = x_s - x_c, dvn = x_c - x_n,
-// dzs / dzn = east - west of u_z on the south / north row.
+// around the node, accumulated onto d = u^m - u^{m-1}: lap = (x_e - x_c) - (x_c - x_w),
+// dvs = x_s - x_c, dvn = x_c - x_n, dzs / dzn = east - west of u_z on the south / north row.
 template <typename real>
-__device__ __forceinline__ real op_x(const FacCoef<real> &K, real lap, real dvs, real dvn, real dzs, real dzn)
+__device__ __forceinline__ real op_x(const FacCoef<real> &K, real d, real lap, real dvs, real dvn, real dzs,
+                                     real dzn)
 {
-    real a = mul_(K.axx, lap);
+    real a = fma_(K.axx, lap, d);
     a = fma_(K.axzp, dvs, a);
     a = fma_(K.naxzm, dvn, a);
     a = fma_(K.px, dzs, a);
@@ -32,20 +31,22 @@ __device__ __forceinline__ real op_x(const FacCoef<real> &K, real lap, real dvs,
 
 // the same for u_z (roles of the components exchanged)
 template <typename real>
-__device__ __forceinline__ real op_z(const FacCoef<real> &K, real lap, real dws, real dwn, real dxs, real dxn)
+__device__ __forceinline__ real op_z(const FacCoef<real> &K, real d, real lap, real dws, real dwn, real dxs,
+                                     real dxn)
 {
-    real a = mul_(K.azx, lap);
+    real a = fma_(K.azx, lap, d);
     a = fma_(K.azzp, dws, a);
     a = fma_(K.nazzm, dwn, a);
     a = fma_(K.pz, dxs, a);
     return fma_(K.nqz, dxn, a);
 }
 
-// u^{m+1} = u^m + ((u^m - u^{m-1}) + A): the only rounding at the scale of u is the last
+// u^{m+1} = u^m + ((u^m - u^{m-1}) + A), with A accumulated onto u^m - u^{m-1} (op_x,
+// op_z): every rounding before the last is at the scale of the increment, not of u
 template <typename real>
-__device__ __forceinline__ real leap(real u, real um, real A)
+__device__ __forceinline__ real leap(real u, real dA)
 {
-    return u + ((u - um) + A);
+    return u + dA;
 }
 
 // first-order absorbing node, forward in time: u + c dt/h (u_inward - u)
@@ -83,8 +84,8 @@ __device__ __forceinline__ void node_update(const FacCoef<real> &K, const real *
     const real *xr = top ? xc : xn, *zr = top ? zc : zn;   // top: dv_n = 0, cross terms on row 0
     const real lx = (xc[2] - xc[1]) - (xc[1] - xc[0]);
     const real lz = (zc[2] - zc[1]) - (zc[1] - zc[0]);
-    ux = leap(xc[1], xm, op_x(K, lx, xs[1] - xc[1], xc[1] - xr[1], zs[2] - zs[0], zr[2] - zr[0]));
-    uz = leap(zc[1], zm, op_z(K, lz, zs[1] - zc[1], zc[1] - zr[1], xs[2] - xs[0], xr[2] - xr[0]));
+    ux = leap(xc[1], op_x(K, xc[1] - xm, lx, xs[1] - xc[1], xc[1] - xr[1], zs[2] - zs[0], zr[2] - zr[0]));
+    uz = leap(zc[1], op_z(K, zc[1] - zm, lz, zs[1] - zc[1], zc[1] - zr[1], xs[2] - xs[0], xr[2] - xr[0]));
 }
 
 // ------------------------------------------------------------------------------
@@ -135,10 +136,10 @@ __device__ __forceinline__ void south(Row2 &c, const Row2 &s)
 __device__ __forceinline__ void pair_update(const FacCoef<float> &K, const Row2 &n, const Row2 &c,
                                             const Row2 &s, float4 &u)
 {
-    u.x = leap(c.xa, u.x, op_x(K, c.lxa, c.vxa, n.vxa, s.dza, n.dza));
-    u.z = leap(c.xb, u.z, op_x(K, c.lxb, c.vxb, n.vxb, s.dzb, n.dzb));
-    u.y = leap(c.za, u.y, op_z(K, c.lza, c.vza, n.vza, s.dxa, n.dxa));
-    u.w = leap(c.zb, u.w, op_z(K, c.lzb, c.vzb, n.vzb, s.dxb, n.dxb));
+    u.x = leap(c.xa, op_x(K, c.xa - u.x, c.lxa, c.vxa, n.vxa, s.dza, n.dza));
+    u.z = leap(c.xb, op_x(K, c.xb - u.z, c.lxb, c.vxb, n.vxb, s.dzb, n.dzb));
+    u.y = leap(c.za, op_z(K, c.za - u.y, c.lza, c.vza, n.vza, s.dxa, n.dxa));
+    u.w = leap(c.zb, op_z(K, c.zb - u.w, c.lzb, c.vzb, n.vzb, s.dxb, n.dxb));
 }
 
 // Absorbing rows: the bottom row from its north neighbour, then the side columns
