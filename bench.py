@@ -589,8 +589,8 @@ def streaming_roofline(kname, ms_per_launch, cells_per_launch, bpc=24):
     return {"bound": "hbm", "kernel": kname, "achieved": gbs, "peak": peak, "peak_kind": peak_kind,
             "unit": "GB/s", "frac": gbs / peak, "algorithmic_bytes_per_cell_update": bpc,
             "traffic": (tb * cells_per_launch if tb is not None else None),
-            "traffic_note": "committed ncu DRAM bytes per cell-update of the same code (401x201 capture) "
-                            "x the cell-updates of one launch",
+            "traffic_note": "committed ncu DRAM bytes per cell-update of the same code (one-pass capture "
+                            "named in profiles/stencil_dram_traffic.json) x the cell-updates of one launch",
             "launch_ms": ms_per_launch}
 
 
