@@ -85,10 +85,13 @@ static Sizes sizes(const Geometry &g, int precision, int max_solves)
     const int chunk = std::max(1, max_solves / kND);   // the larger of the two node chunks
     Sizes s;
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    s.u = al((size_t)max_solves * g.solve_stride * e);
     // FP32 grids that do not fit on chip keep a second pair of levels for the two-step
-    // kernel (it reads one pair and writes the other)
-    s.u2 = (precision == OED_FP32 && !resident_fits(g)) ? 2 * s.u : 0;
+    // kernel (it reads one pair and writes the other), whose paired layout may need a
+    // little more than the planar one per solve
+    const bool two_step = precision == OED_FP32 && !resident_fits(g);
+    const size_t per = two_step ? std::max(g.solve_stride, paired_stride(g)) : g.solve_stride;
+    s.u = al((size_t)max_solves * per * e);
+    s.u2 = two_step ? 2 * s.u : 0;
     s.kp = s.u2 ? al((size_t)g.nz * 16 * sizeof(float)) : 0;   // packed row coefficients
     s.src = al((size_t)max_solves * (precision == OED_FP64 ? sizeof(SourceDesc<double>)
                                                            : sizeof(SourceDesc<float>)));

@@ -84,6 +84,13 @@ struct Geometry {
     size_t solve_stride;   // 2 * comp_stride
 };
 
+// The paired level layout of the two-step TMA kernel (FP32): row z of a solve holds the
+// even columns' (x, z) in sq float2 slots, then the odd columns' in sq more; column c sits
+// in slot (c >> 1) + 2 of its half, and the slots of columns -4 .. -1 and past nx - 1 are
+// zero.  sq is even, so each half row is a multiple of 16 bytes (a TMA stride).
+__host__ __device__ inline int paired_sq(const Geometry &g) { return ((g.nx + 1) / 2 + 4 + 1) & ~1; }
+__host__ __device__ inline size_t paired_stride(const Geometry &g) { return (size_t)g.nz * 4 * paired_sq(g); }
+
 struct StepTuning {
     int zs;      // streaming kernel: rows marched per thread
     int wz;      // streaming kernel: warps along z in a block
@@ -174,6 +181,7 @@ int tma2_prepare(oed_ctx *ctx);
 void launch_pack_kp(const oed_ctx *ctx, cudaStream_t st);
 cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
                               int nsteps_override, const float **last);
+void launch_tma2_gather(const oed_ctx *ctx, int nsolve, const float *last, int m, cudaStream_t st);
 
 // resident.cu
 int resident_cluster_size(const oed_ctx *ctx);

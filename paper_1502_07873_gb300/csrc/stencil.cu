@@ -226,19 +226,21 @@ void launch_step_probe(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st
 cudaError_t launch_forward_steps(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0,
                                  cudaEvent_t ev1)
 {
-    const size_t bytes = (size_t)nsolve * ctx->g.solve_stride * ctx->elem;
-    cudaMemsetAsync(ctx->d_u0, 0, bytes, st);
-    cudaMemsetAsync(ctx->d_u1, 0, bytes, st);
-    if (ctx->tune.C == -2) {
-        cudaMemsetAsync(ctx->d_u2, 0, bytes, st);
-        cudaMemsetAsync(ctx->d_u3, 0, bytes, st);
+    if (ctx->tune.C == -2) {   // the two-step kernel's paired layout
+        const size_t pb = (size_t)nsolve * paired_stride(ctx->g) * sizeof(float);
+        cudaMemsetAsync(ctx->d_u0, 0, pb, st);
+        cudaMemsetAsync(ctx->d_u1, 0, pb, st);
+        cudaMemsetAsync(ctx->d_u2, 0, pb, st);
+        cudaMemsetAsync(ctx->d_u3, 0, pb, st);
         const float *last = nullptr;
         const cudaError_t e = launch_steps_tma2(ctx, nsolve, st, ev0, ev1, 0, &last);
         if (e != cudaSuccess) return e;
-        k_gather<float><<<nsolve, 128, 0, st>>>(last, (float *)ctx->d_trace, ctx->d_rec, ctx->g, ctx->g.nsteps,
-                                                nsolve);
+        launch_tma2_gather(ctx, nsolve, last, ctx->g.nsteps, st);
         return cudaGetLastError();
     }
+    const size_t bytes = (size_t)nsolve * ctx->g.solve_stride * ctx->elem;
+    cudaMemsetAsync(ctx->d_u0, 0, bytes, st);
+    cudaMemsetAsync(ctx->d_u1, 0, bytes, st);
     if (ctx->tune.C == -1) {
         const cudaError_t e = launch_steps_tma(ctx, nsolve, st, ev0, ev1, 0);
         if (e != cudaSuccess) return e;

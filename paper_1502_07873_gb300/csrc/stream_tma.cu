@@ -271,6 +271,20 @@ bool tma_make_map(CUtensorMap *map, void *base, const Geometry &g, int nsolve, i
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool tma_make_paired_map(CUtensorMap *map, void *base, const Geometry &g, int nsolve, int bslots, int bz)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const int sq = paired_sq(g);
+    const cuuint64_t dims[4] = {(cuuint64_t)(2 * sq), 2, (cuuint64_t)g.nz, (cuuint64_t)nsolve};
+    const cuuint64_t strides[3] = {(cuuint64_t)sq * 8, (cuuint64_t)sq * 16, (cuuint64_t)paired_stride(g) * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * bslots), 2, (cuuint32_t)bz, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_wait_selftest(const oed_ctx *ctx, unsigned long long limit_ns, cudaStream_t st)
 {
     k_wait_selftest<<<1, 32, 0, st>>>(ctx->d_err, limit_ns);

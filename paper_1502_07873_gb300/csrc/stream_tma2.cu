@@ -2,26 +2,30 @@
 // cluster-resident kernel (Sec. 3.3.1, Eq. Full_Disc; the packed node update of
 // pair_math.cuh, so the bits are those of every other stencil kernel).
 //
-// A persistent CTA walks tiles (solve, 20-row band, 60-column band).  For each tile
-// its producer warp loads, with cp.async.bulk.tensor, into one stage of a 4-stage
-// shared-memory ring:
-//   HM  u^m,     x and z planes, rows z0-2 .. z0+21, columns x0-4 .. x0+63
-//   HP  u^{m-1}, x and z planes, rows z0-1 .. z0+20, columns x0-4 .. x0+63
+// The levels are kept in the paired layout (oed_internal.cuh): a row holds the even
+// columns' (x, z) pairs, then the odd columns', as the cluster-resident kernel keeps its
+// rows in shared memory.  A persistent CTA walks tiles (solve, 20-row band, 60-column
+// band).  For each tile its producer warp loads, with one 4-D cp.async.bulk.tensor copy
+// per level (34 slots of both halves, i.e. columns x0-4 .. x0+63, by the rows below),
+// into one stage of a 4-stage shared-memory ring:
+//   HM  u^m,     rows z0-2 .. z0+21
+//   HP  u^{m-1}, rows z0-1 .. z0+20
 // and, with cp.async.bulk, the coefficient rows z0-1 .. z0+20 that lie in the grid, as
 // (x, z) pairs packed once per problem
-// (x0 is a multiple of 60, so every x start is a multiple of four floats and every
-// copy starts on a 16-byte boundary; rows and columns outside the grid read as
-// zeros and are never used).  Completion is tracked per stage by an mbarrier with
-// the stage's byte count.  Two groups of four consumer warps take the tiles in turn,
-// each owning two stages.  In a tile, lane p owns the column pair x0-2+2p and a warp
-// a segment of rows (the tests for the surface and bottom rows, the side columns and
-// the source patch run only in the tiles that hold them):
+// (x0 is a multiple of 60, so every copy starts on a 16-byte boundary; rows and
+// columns outside the grid read as zeros and are never used).  Completion is tracked
+// per stage by an mbarrier with the stage's byte count.  Two groups of four consumer
+// warps take the tiles in turn, each owning two stages.  In a tile, lane p owns the
+// column pair x0-2+2p and reads its pair, its west and its east column as four
+// conflict-free 64-bit (x, z) loads, and a warp a segment of rows (the tests for the
+// surface and bottom rows, the side columns and the source patch run only in the
+// tiles that hold them):
 //   step 1  u^{m+1} on rows z0-1 .. z0+20, columns x0-2 .. x0+61 (the tile and a
 //           one-node ring), written in place over u^{m-1} in HP (a node reads only
 //           its own u^{m-1}), and, for the tile's own nodes, to global memory;
 //   group barrier (the ring values of other warps' rows are needed next);
 //   step 2  u^{m+2} on the tile's own nodes, from u^{m+1} in HP and u^m in HM, to
-//           global memory.
+//           global memory (skipped in the single-step pass of an odd step count).
 // The receiver samples of levels m and m+1 are taken from HM and HP on the surface
 // band.  Levels live in two pairs of buffers used in alternation: a pass reads
 // (u^{m-1}, u^m) from one pair and writes (u^{m+1}, u^{m+2}) to the other, so no
@@ -38,17 +42,18 @@
 namespace oed {
 
 constexpr int kT2X = 60, kT2Z = 20;                  // output tile
-constexpr int kW2X = kT2X + 8;                       // 68 columns: x0-4 .. x0+63
+constexpr int kS2 = (kT2X + 8) / 2;                  // 34 slots per half row: columns x0-4 .. x0+63
+constexpr int kR2 = 2 * kS2;                         // float2 slots per tile row
 constexpr int kM2Z = kT2Z + 4;                       // 24 rows of u^m: z0-2 .. z0+21
 constexpr int kP2Z = kT2Z + 2;                       // 22 rows of u^{m-1}, u^{m+1}: z0-1 .. z0+20
 constexpr int k2Groups = 2, k2GroupStages = 2, k2Stages = k2Groups * k2GroupStages;
 constexpr int k2GroupWarps = 4, k2ConsumerWarps = k2Groups * k2GroupWarps;
-constexpr int k2PlaneM = kW2X * kM2Z * 4;                       // 6528 = 51 x 128
-constexpr int k2PlaneP = kW2X * kP2Z * 4;                       // 5984
-constexpr int k2PlanePPad = (k2PlaneP + 127) / 128 * 128;       // 6016
+constexpr int k2PlaneM = kR2 * kM2Z * 8;                        // 13056 = 102 x 128
+constexpr int k2PlaneP = kR2 * kP2Z * 8;                        // 11968
+constexpr int k2PlanePPad = (k2PlaneP + 127) / 128 * 128;       // 12032
 constexpr int k2Coef = kP2Z * (int)sizeof(KP);                  // 1408
-constexpr int k2StageBytes = 2 * k2PlaneM + 2 * k2PlanePPad + k2Coef;
-constexpr unsigned k2TileTx = 2 * k2PlaneM + 2 * k2PlaneP;
+constexpr int k2StageBytes = k2PlaneM + k2PlanePPad + k2Coef;
+constexpr unsigned k2TileTx = k2PlaneM + k2PlaneP;
 constexpr int k2SmemBytes = k2Stages * k2StageBytes + 128 /* alignment slack */ + 128 /* barriers */;
 // rows of step 1 per warp (22 = 6 + 6 + 5 + 5) and of step 2 (20 = 4 x 5)
 __device__ __constant__ int k2Seg1[k2GroupWarps + 1] = {0, 6, 12, 17, 22};
@@ -56,8 +61,8 @@ constexpr int k2Seg1Max = 6;
 constexpr int k2Rows2 = kT2Z / k2GroupWarps;
 
 struct Tma2Args {
-    float *outA;                  // u^{m+1} (global, the other pair's older level)
-    float *outB;                  // u^{m+2} (global, the other pair's newer level)
+    float *outA;                  // u^{m+1} (global, paired layout, the other pair's older level)
+    float *outB;                  // u^{m+2} (global, paired layout, the other pair's newer level)
     const KP *kp;                 // [nz] the rows' coefficients as (x, z) pairs
     const SourceDesc<float> *src;
     const float *stf;
@@ -66,6 +71,9 @@ struct Tma2Args {
     int *err;
     Geometry g;
     int m, nsolve, nbx, nbz;
+    int sq;                       // slots per half row of the paired layout
+    size_t pst;                   // floats per solve of the paired layout
+    int single;                   // 1: step 1 only (the last pass of an odd step count)
 };
 
 __device__ __forceinline__ int stage2(unsigned k)
@@ -77,26 +85,31 @@ __device__ __forceinline__ unsigned phase2(unsigned k)
     return ((k / k2Groups) / k2GroupStages) & 1u;
 }
 
-// a row of the (x, z) planes px, pz (kW2X floats per row) seen by the pair at column
-// offset q: its two columns, the west and the east column
-__device__ __forceinline__ void plane_row(const float *px, const float *pz, int r, int q, Row2P &row)
+// q points at a lane's even slot in a tile row: its pair is (q[0], q[kS2]), its west
+// column q[kS2 - 1] (odd half), its east column q[1] (even half); 64-bit loads at an
+// 8-byte stride across the warp, no bank conflicts
+__device__ __forceinline__ void tile_row(const float2 *q, Row2P &row)
 {
-    const float *ax = px + r * kW2X + q, *az = pz + r * kW2X + q;
-    const float2 mx = *reinterpret_cast<const float2 *>(ax), mz = *reinterpret_cast<const float2 *>(az);
-    row_fromP(make_float2(ax[-1], az[-1]), make_float4(mx.x, mz.x, mx.y, mz.y), make_float2(ax[2], az[2]), row);
+    const float2 e = q[0], o = q[kS2];
+    row_fromP(q[kS2 - 1], make_float4(e.x, e.y, o.x, o.y), q[1], row);
 }
 
-__device__ __forceinline__ float4 plane_pair(const float *px, const float *pz, int r, int q)
+__device__ __forceinline__ float4 tile_pair(const float2 *q)
 {
-    const float2 x = *reinterpret_cast<const float2 *>(px + r * kW2X + q);
-    const float2 z = *reinterpret_cast<const float2 *>(pz + r * kW2X + q);
-    return make_float4(x.x, z.x, x.y, z.y);
+    const float2 e = q[0], o = q[kS2];
+    return make_float4(e.x, e.y, o.x, o.y);
 }
 
-__device__ __forceinline__ void plane_put(float *px, float *pz, int r, int q, float4 u)
+__device__ __forceinline__ void tile_put(float2 *q, float4 u)
 {
-    *reinterpret_cast<float2 *>(px + r * kW2X + q) = make_float2(u.x, u.z);
-    *reinterpret_cast<float2 *>(pz + r * kW2X + q) = make_float2(u.y, u.w);
+    q[0] = make_float2(u.x, u.y);
+    q[kS2] = make_float2(u.z, u.w);
+}
+
+// float offset of (column x, component comp) in a tile row whose first column is x0 - 4
+__device__ __forceinline__ int tile_off(int x, int x0, int comp)
+{
+    return 2 * ((x & 1) * kS2 + (x >> 1) + 2 - (x0 >> 1)) + comp;
 }
 
 // One node-pair update at grid row z: the interior, surface or bottom form, the
@@ -203,12 +216,12 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
                 const int c0 = max(0, z0 - 1), c1 = min(g.nz, z0 + kT2Z + 1);
                 const unsigned cbytes = (unsigned)((c1 - c0) * (int)sizeof(KP));
                 mbar_expect_tx(&full_bar[stage], k2TileTx + cbytes);
-                tma_load3(st, &cur_m, x0 - 4, z0 - 2, 2 * s, &full_bar[stage]);
-                tma_load3(st + k2PlaneM, &cur_m, x0 - 4, z0 - 2, 2 * s + 1, &full_bar[stage]);
-                tma_load3(st + 2 * k2PlaneM, &cur_p, x0 - 4, z0 - 1, 2 * s, &full_bar[stage]);
-                tma_load3(st + 2 * k2PlaneM + k2PlanePPad, &cur_p, x0 - 4, z0 - 1, 2 * s + 1, &full_bar[stage]);
-                bulk_load(st + 2 * k2PlaneM + 2 * k2PlanePPad + (c0 - (z0 - 1)) * (int)sizeof(KP), a.kp + c0,
-                          cbytes, &full_bar[stage]);
+                // slot x0 / 2 of each half is column x0 - 4: the float coordinate x0 is a
+                // multiple of four, a 16-byte boundary
+                tma_load4(st, &cur_m, x0, 0, z0 - 2, s, &full_bar[stage]);
+                tma_load4(st + k2PlaneM, &cur_p, x0, 0, z0 - 1, s, &full_bar[stage]);
+                bulk_load(st + k2PlaneM + k2PlanePPad + (c0 - (z0 - 1)) * (int)sizeof(KP), a.kp + c0, cbytes,
+                          &full_bar[stage]);
             }
             if (!ok) {
                 atomicExch(a.err, 1);
@@ -222,7 +235,7 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
 
     const int grp = (warp - 1) / k2GroupWarps, wig = (warp - 1) % k2GroupWarps;
     const int gt = wig * 32 + lane;
-    const int q = 2 + 2 * lane;   // plane column of the pair's first column
+    const size_t grow = 4 * (size_t)a.sq;   // floats per row of the paired layout
     for (unsigned k = grp, t = blockIdx.x + grp * gridDim.x; t < ntile; k += k2Groups, t += k2Groups * gridDim.x) {
         const int stage = stage2(k);
         // the group leaves together or not at all: one thread's wait may run out while
@@ -238,15 +251,16 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
         const int bz = (int)(qq - (unsigned)s * (unsigned)a.nbz);
         const int x0 = bx * kT2X, z0 = bz * kT2Z;
         unsigned char *st = smem + stage * k2StageBytes;
-        const float *hmx = reinterpret_cast<const float *>(st);
-        const float *hmz = hmx + k2PlaneM / 4;
-        float *hpx = reinterpret_cast<float *>(st + 2 * k2PlaneM);
-        float *hpz = hpx + k2PlanePPad / 4;
-        const KP *kp = reinterpret_cast<const KP *>(st + 2 * k2PlaneM + 2 * k2PlanePPad);
+        const float2 *hm = reinterpret_cast<const float2 *>(st);
+        float2 *hp = reinterpret_cast<float2 *>(st + k2PlaneM);
+        const KP *kp = reinterpret_cast<const KP *>(st + k2PlaneM + k2PlanePPad);
+        const float2 *hmq = hm + lane + 1;   // this lane's even slot in tile row 0
+        float2 *hpq = hp + lane + 1;
         const SourceDesc<float> *sd = a.src + s;
-        float *gAx = a.outA + (size_t)s * g.solve_stride, *gAz = gAx + g.comp_stride;
-        float *gBx = a.outB + (size_t)s * g.solve_stride, *gBz = gBx + g.comp_stride;
         const int c = x0 - 2 + 2 * lane;   // the pair's first column
+        // the pair's even slot in row 0 of the solve's outputs (its odd slot is sq float2 on)
+        const size_t co = (size_t)s * a.pst + 2 * (size_t)((c >> 1) + 2);
+        float *gA = a.outA + co, *gB = a.outB + co;
         const int si0 = sd->i0, sj0 = sd->j0;
         // tile-uniform flags: the tile (with its ring) holds the surface or bottom row, a
         // side column, or part of the source patch; the tests of each are skipped
@@ -260,9 +274,10 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
         // receiver samples of level m (HM row 2 is grid row 0 on the surface band)
         if (z0 == 0)
             for (int r = gt; r < 2 * g.nrec; r += 32 * k2GroupWarps) {
-                const int xr = a.rec[r >> 1] - x0;
-                if (xr >= 0 && xr < kT2X)
-                    a.trace[tr0 + (size_t)a.m * g.nrec * 2 + r] = ((r & 1) ? hmz : hmx)[2 * kW2X + xr + 4];
+                const int xr = a.rec[r >> 1];
+                if (xr >= x0 && xr < x0 + kT2X)
+                    a.trace[tr0 + (size_t)a.m * g.nrec * 2 + r] =
+                        reinterpret_cast<const float *>(hm + 2 * kR2)[tile_off(xr, x0, r & 1)];
             }
         const bool valid = c >= 0 && c < g.nx;
         PairCtx pc;
@@ -280,8 +295,8 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
         if (valid) {
             const int ra = k2Seg1[wig], nr = k2Seg1[wig + 1] - ra;
             Row2P rn, rc, rs;
-            plane_row(hmx, hmz, ra, q, rn);       // HM row r is grid row z0 - 2 + r
-            plane_row(hmx, hmz, ra + 1, q, rc);
+            tile_row(hmq + ra * kR2, rn);       // HM row r is grid row z0 - 2 + r
+            tile_row(hmq + (ra + 1) * kR2, rc);
             southP(rn, rc);
             // unrolled to the longest segment, so the window rows stay in place in the
             // registers instead of being copied row after row
@@ -290,16 +305,16 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
                 if (i >= nr) break;
                 const int r = ra + i;
                 const int z = z0 - 1 + r;
-                plane_row(hmx, hmz, r + 2, q, rs);
+                tile_row(hmq + (r + 2) * kR2, rs);
                 southP(rc, rs);
                 if (z >= 0 && z < g.nz) {
-                    float4 u = plane_pair(hpx, hpz, r, q);
+                    float4 u = tile_pair(hpq + r * kR2);
                     update_at(kp[r], z, g.nz, rn, rc, rs, pc, tf, sd, S1, u);
-                    plane_put(hpx, hpz, r, q, u);
+                    tile_put(hpq + r * kR2, u);
                     if (own && r >= 1 && r <= kT2Z) {
-                        const size_t o = (size_t)z * g.xp + c;
-                        __stcs(reinterpret_cast<float2 *>(gAx + o), make_float2(u.x, u.z));
-                        __stcs(reinterpret_cast<float2 *>(gAz + o), make_float2(u.y, u.w));
+                        float *o = gA + (size_t)z * grow;
+                        __stcs(reinterpret_cast<float2 *>(o), make_float2(u.x, u.y));
+                        __stcs(reinterpret_cast<float2 *>(o + 2 * a.sq), make_float2(u.z, u.w));
                     }
                 }
                 rn = rc;
@@ -310,28 +325,29 @@ __global__ void __launch_bounds__(32 * (k2ConsumerWarps + 1), 2)
         // receiver samples of level m+1 (HP row 1 is grid row 0)
         if (z0 == 0)
             for (int r = gt; r < 2 * g.nrec; r += 32 * k2GroupWarps) {
-                const int xr = a.rec[r >> 1] - x0;
-                if (xr >= 0 && xr < kT2X)
-                    a.trace[tr0 + (size_t)(a.m + 1) * g.nrec * 2 + r] = ((r & 1) ? hpz : hpx)[kW2X + xr + 4];
+                const int xr = a.rec[r >> 1];
+                if (xr >= x0 && xr < x0 + kT2X)
+                    a.trace[tr0 + (size_t)(a.m + 1) * g.nrec * 2 + r] =
+                        reinterpret_cast<const float *>(hp + kR2)[tile_off(xr, x0, r & 1)];
             }
         // step 2: u^{m+2} on the tile's rows [5 wig, 5 wig + 5) (grid row z0 + r)
-        if (own) {
+        if (own && !a.single) {
             const int ra = wig * k2Rows2;
             Row2P rn, rc, rs;
-            plane_row(hpx, hpz, ra, q, rn);       // HP row r + 1 is grid row z0 + r
-            plane_row(hpx, hpz, ra + 1, q, rc);
+            tile_row(hpq + ra * kR2, rn);       // HP row r + 1 is grid row z0 + r
+            tile_row(hpq + (ra + 1) * kR2, rc);
             southP(rn, rc);
 #pragma unroll
             for (int r = ra; r < ra + k2Rows2; r++) {
                 const int z = z0 + r;
                 if (z >= g.nz) break;
-                plane_row(hpx, hpz, r + 2, q, rs);
+                tile_row(hpq + (r + 2) * kR2, rs);
                 southP(rc, rs);
-                float4 u = plane_pair(hmx, hmz, r + 2, q);   // u^m of the node
+                float4 u = tile_pair(hmq + (r + 2) * kR2);   // u^m of the node
                 update_at(kp[r + 1], z, g.nz, rn, rc, rs, pc, tf, sd, S2, u);
-                const size_t o = (size_t)z * g.xp + c;
-                __stcs(reinterpret_cast<float2 *>(gBx + o), make_float2(u.x, u.z));
-                __stcs(reinterpret_cast<float2 *>(gBz + o), make_float2(u.y, u.w));
+                float *o = gB + (size_t)z * grow;
+                __stcs(reinterpret_cast<float2 *>(o), make_float2(u.x, u.y));
+                __stcs(reinterpret_cast<float2 *>(o + 2 * a.sq), make_float2(u.z, u.w));
                 rn = rc;
                 rc = rs;
             }
@@ -372,10 +388,30 @@ int tma2_prepare(oed_ctx *ctx)
     return ctx->tma2_ctas;
 }
 
+// Receiver samples of one level in the paired layout (the final level after the last pass).
+__global__ void k_gather_paired(const float *__restrict__ cur, float *__restrict__ trace,
+                                const int *__restrict__ rec, Geometry g, int sq, size_t pst, int m, int nsolve)
+{
+    const int s = blockIdx.x;
+    if (s >= nsolve) return;
+    const float *row0 = cur + (size_t)s * pst;   // grid row 0
+    float *tr = trace + ((size_t)s * g.nlev + m) * g.nrec * 2;
+    for (int q = threadIdx.x; q < 2 * g.nrec; q += blockDim.x) {
+        const int x = rec[q >> 1];
+        tr[q] = row0[2 * ((x & 1) * sq + (x >> 1) + 2) + (q & 1)];
+    }
+}
+
+void launch_tma2_gather(const oed_ctx *ctx, int nsolve, const float *last, int m, cudaStream_t st)
+{
+    k_gather_paired<<<nsolve, 128, 0, st>>>(last, (float *)ctx->d_trace, ctx->d_rec, ctx->g, paired_sq(ctx->g),
+                                            paired_stride(ctx->g), m, nsolve);
+}
+
 // nsteps (or nsteps_override) steps of nsolve solves: two-step passes over the level
-// pairs (d_u0, d_u1) and (d_u2, d_u3) in alternation, and a last one-step launch of the
-// one-step TMA kernel when the count is odd.  *last is set to the buffer that holds the
-// final level.  The caller zeroes all four levels.
+// pairs (d_u0, d_u1) and (d_u2, d_u3) in alternation, all in the paired layout, and a
+// last single-step pass when the count is odd.  *last is set to the buffer that holds
+// the final level.  The caller zeroes all four levels (paired_stride floats per solve).
 cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
                               int nsteps_override, const float **last)
 {
@@ -384,8 +420,8 @@ cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, c
     float *lv[4] = {(float *)ctx->d_u0, (float *)ctx->d_u1, (float *)ctx->d_u2, (float *)ctx->d_u3};
     CUtensorMap mmap[2], pmap[2];   // per pair: u^m (newer level, 2-row halo), u^{m-1} (older, 1-row)
     for (int pr = 0; pr < 2; pr++)
-        if (!tma_make_map(&mmap[pr], lv[2 * pr + 1], g, nsolve, kW2X, kM2Z) ||
-            !tma_make_map(&pmap[pr], lv[2 * pr], g, nsolve, kW2X, kP2Z))
+        if (!tma_make_paired_map(&mmap[pr], lv[2 * pr + 1], g, nsolve, kS2, kM2Z) ||
+            !tma_make_paired_map(&pmap[pr], lv[2 * pr], g, nsolve, kS2, kP2Z))
             return cudaErrorInvalidValue;
     Tma2Args a;
     a.kp = (const KP *)ctx->d_kp;
@@ -398,6 +434,9 @@ cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, c
     a.nsolve = nsolve;
     a.nbx = (g.nx + kT2X - 1) / kT2X;
     a.nbz = (g.nz + kT2Z - 1) / kT2Z;
+    a.sq = paired_sq(g);
+    a.pst = paired_stride(g);
+    a.single = 0;
     const long long ntile = (long long)nsolve * a.nbx * a.nbz;
     if (ntile >= (1LL << 31) - 2LL * ctx->tma2_ctas) return cudaErrorInvalidValue;   // 32-bit tile indices
     const int grid = (int)(ntile < (long long)ctx->tma2_ctas ? ntile : (long long)ctx->tma2_ctas);
@@ -405,17 +444,13 @@ cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, c
     tma_record(ev0, st);
     int pr = 0;   // the pair holding (u^{m-1}, u^m)
     int m = 0;
-    for (; m + 2 <= nsteps; m += 2, pr ^= 1) {
+    for (; m < nsteps; m += 2, pr ^= 1) {
         a.outA = lv[2 * (pr ^ 1)];
         a.outB = lv[2 * (pr ^ 1) + 1];
         a.m = m;
+        a.single = m + 1 == nsteps;   // an odd count: the last pass takes one step
         k_step2_tma<<<grid, 32 * (k2ConsumerWarps + 1), k2SmemBytes, st>>>(a, mmap[pr], pmap[pr]);
-    }
-    *last = lv[2 * pr + 1];
-    if (m < nsteps) {   // an odd count: the last step in place over the older level
-        const cudaError_t e = launch_tma_one_step(ctx, nsolve, st, lv[2 * pr + 1], lv[2 * pr], m);
-        if (e != cudaSuccess) return e;
-        *last = lv[2 * pr];
+        *last = a.single ? a.outA : a.outB;
     }
     tma_record(ev1, st);
     return cudaGetLastError();

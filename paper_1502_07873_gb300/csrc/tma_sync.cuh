@@ -16,6 +16,11 @@ namespace oed {
 // copy boxes of bx columns by bz rows (stream_tma.cu)
 bool tma_make_map(CUtensorMap *map, void *base, const Geometry &g, int nsolve, int bx, int bz);
 
+// host: tensor map over one level in the paired layout (oed_internal.cuh), as a 4-D tensor
+// (floats of a half row, the two halves, rows, solves), copy boxes of bslots slots of both
+// halves by bz rows (stream_tma.cu)
+bool tma_make_paired_map(CUtensorMap *map, void *base, const Geometry &g, int nsolve, int bslots, int bz);
+
 constexpr unsigned long long kWaitLimitNs = 2000000000ULL;   // 2 s per wait
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
@@ -70,6 +75,17 @@ __device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, int
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
             "r"((unsigned)__cvta_generic_to_shared(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z),
+        "r"((unsigned)__cvta_generic_to_shared(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load4(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
+            "r"((unsigned)__cvta_generic_to_shared(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w),
         "r"((unsigned)__cvta_generic_to_shared(bar))
         : "memory");
 }

@@ -494,6 +494,29 @@ def test_tma_kernel_many_tiles_per_cta_bitwise(P):
     assert float(g_ref.abs().max()) > 1e-3
 
 
+def test_resident_source_patch_across_slabs_bitwise(P):
+    """The source term of the cluster-resident kernel is added by the edge warp after the march
+    warps that own patch nodes arrive at a named barrier.  Patches that straddle a CTA's slab
+    boundary (each CTA adds its own rows) or a row-segment boundary (two groups of march warps
+    arrive), at clusters of 6, 7 and 8 CTAs (slabs of 34, 29 and 26 rows, segments of about a
+    third of a slab), bit for bit against the register streaming kernel."""
+    w = W.tiny(nx=401, nz=201, h=5.0, nsteps=480, nrec=12)
+    lo = np.array(w.prior_lo)
+    depths = [510.0, 570.0, 402.5, 595.0, 436.0, 468.0, 532.0, 451.0]   # rows 102, 114, 80, ...
+    th = np.array([[800.0 + 50.0 * k, d, lo[2], 6.0, 5e13, 2e13, 7e13] for k, d in enumerate(depths)])
+    ctx = P.Context(P.problem_from_workload(w, P.OED_FP32), max_solves=len(depths))
+    ctx.set_tuning(0, 4, 4)
+    g_ref = torch.empty((len(depths), w.nlevels, w.nrec, 2), dtype=torch.float64, device=DEV)
+    P.oed_forward(ctx, _t(th), g_ref)
+    for C in (6, 7, 8):
+        ctx.set_tuning(C, 4, 4)
+        g = torch.empty_like(g_ref)
+        P.oed_forward(ctx, _t(th), g)
+        torch.cuda.synchronize()
+        assert torch.equal(g, g_ref), C
+    assert float(g_ref.abs().max()) > 1e-3
+
+
 def test_resident_one_row_per_cta(P, oracle):
     """Eight CTAs of one row each (nz = 8, clusters of 8): the surface row's south row, every
     north and south row and the absorbing bottom row's north row come from neighbouring CTAs'
