@@ -27,10 +27,11 @@
 // The surface row, the bottom row and the rows whose neighbour lives in another
 // CTA are peeled off the main loop, and so are the march's last one to three rows
 // (the only ones that do not prefetch): the unrolled march body has no branch.  The
-// absorbing side columns are left out of the march (its stores to them are
-// predicated off) and written by a separate edge warp from u^m alone, so the warps
-// that hold a side column march exactly like the others; the source term is added
-// after the sweep to the few patch nodes.  The arithmetic runs on packed
+// absorbing side columns are left out of the march (its stores to them go to ghost
+// slots that no thread reads) and written by a separate edge warp from u^m alone, so
+// the warps that hold a side column march exactly like the others; the same warp adds
+// the source term to the patch nodes once the march warps that own them have stored
+// them (named barrier 1).  The arithmetic runs on packed
 // (x, z) pairs (.f32x2).  HBM traffic is only the seismogram samples and the source
 // time function: the wavefield never leaves the chip, so this kernel is bound by
 // shared-memory latency and throughput and the per-step barrier, not by HBM.
