@@ -116,6 +116,8 @@ def parse():
                     help="serving: requests taken from the head of the seeded config-5 stream")
     ap.add_argument("--serving-work", type=float, default=1.2e13,
                     help="serving: bound on the draw's total cell-updates")
+    ap.add_argument("--serving-workers", type=int, default=4,
+                    help="serving: requests the server runs at once (max_active)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the layered, design-sweep and serving sub-objects of the default line")
     return ap.parse_args()
@@ -1064,7 +1066,7 @@ def measure_serving(P, torch, dev, args, rank, n_first=24, work_bound=1.2e13, pl
                 for k, ((t, w), th) in enumerate(zip(draw, thetas))]
 
     items = served_items()
-    srv = P.Server(200 << 30, max_active=4, chunk_nodes=chunk)
+    srv = P.Server(200 << 30, max_active=args.serving_workers, chunk_nodes=chunk)
     # warm the per-shape tuning cache outside the timed streams: for each grid shape a
     # request of a full chunk of nodes and a few steps (the launch shape depends on the
     # grid and the batch, not on the step count)
@@ -1162,7 +1164,7 @@ def measure_serving(P, torch, dev, args, rank, n_first=24, work_bound=1.2e13, pl
             "plain_fp64_one_at_a_time": plain,
             "served_vs_plain_max_rel_dkl": max(dkl_rel), "served_vs_plain_median_rel_dkl": float(np.median(dkl_rel)),
             "accuracy_nodes": len(dkl_rel), "clocks": clk.summary(),
-            "server": "max_active 4, chunk 256 nodes, budget 200 GiB, pooled workspaces, admission past a "
+            "server": f"max_active {args.serving_workers}, chunk 256 nodes, budget 200 GiB, pooled workspaces, admission past a "
                       "blocked head within 10 s"}
 
 
