@@ -133,18 +133,22 @@ const char *oed_status_string(int status);
  *   launches  host [1] or NULL: stencil launches in that interval (0 if none yet) */
 int oed_last_step_time(const oed_ctx *ctx, float *ms, int *launches);
 
-/* Time stepping runs in one of three kernels:
+/* Time stepping runs in one of four kernels:
  *  - streaming: one launch per step over all solves, wavefields in HBM
  *    (any grid, FP32 or FP64), replayed from a captured CUDA graph;
  *  - TMA streaming (FP32): the same, with halo tiles moved by the tensor-memory
  *    accelerator into a persistent CTA's mbarrier ring (cluster_size -1);
+ *  - two-step TMA streaming (FP32, grids that do not fit on chip): two steps per
+ *    pass over a paired level layout (cluster_size -2);
  *  - cluster-resident (FP32, grids whose two time levels fit in the shared
  *    memory of a cluster of C <= 8 CTAs, e.g. 401x201): one launch for all
  *    steps, one thread-block cluster per solve, wavefield kept on chip.
  * All give the same node updates, bit for bit.  oed_autotune times every streaming launch
- * shape (rows marched per thread 2/4/8 x warps per block 1/2/4/8) and every
- * feasible cluster size on nsolve solves of this context's grid, keeps the
- * fastest for later calls, and synchronises the stream.  It overwrites the
+ * shape (rows marched per thread 2/4/8 x warps per block 1/2/4/8), the TMA kernel and
+ * every feasible cluster size on nsolve solves of this context's grid, keeps the
+ * fastest for later calls, and synchronises the stream; where the two-step kernel
+ * runs it is chosen (short probes under-rate it against its rate in a full time
+ * loop).  It overwrites the
  * context's workspace (no caller data).  nsolve in 1..max_solves, typically
  * 15 * oed_chunk_nodes(ctx). */
 int oed_autotune(oed_ctx *ctx, int nsolve, void *stream);

@@ -182,6 +182,7 @@ void launch_pack_kp(const oed_ctx *ctx, cudaStream_t st);
 cudaError_t launch_steps_tma2(const oed_ctx *ctx, int nsolve, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
                               int nsteps_override, const float **last);
 void launch_tma2_gather(const oed_ctx *ctx, int nsolve, const float *last, int m, cudaStream_t st);
+void launch_fill_probe(const oed_ctx *ctx, int nsolve, cudaStream_t st);
 
 // resident.cu
 int resident_cluster_size(const oed_ctx *ctx);

@@ -212,6 +212,33 @@ static void probe_real(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st
     }
 }
 
+// Fill the level buffers the autotuner's probes run on with a deterministic pattern of
+// order-one values (a hash of the index): the probes then time the kernels on data like
+// a running solve's rather than on zeros, on which some kernels run at another speed.
+template <typename real>
+__global__ void k_fill_probe(real *__restrict__ u, size_t n, unsigned salt)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned h = ((unsigned)i ^ salt) * 2654435761u;
+        u[i] = (real)((double)(h >> 8) * (1.0 / 16777216.0) - 0.5);
+    }
+}
+
+void launch_fill_probe(const oed_ctx *ctx, int nsolve, cudaStream_t st)
+{
+    size_t per = ctx->g.solve_stride;
+    if (ctx->d_u2) per = per > paired_stride(ctx->g) ? per : paired_stride(ctx->g);
+    const size_t n = (size_t)nsolve * per;
+    void *lv[4] = {ctx->d_u0, ctx->d_u1, ctx->d_u2, ctx->d_u3};
+    for (int k = 0; k < 4; k++) {
+        if (!lv[k]) continue;
+        if (ctx->precision == OED_FP64)
+            k_fill_probe<double><<<152 * 8, 256, 0, st>>>((double *)lv[k], n, 0x9e3779b9u * (k + 1));
+        else
+            k_fill_probe<float><<<152 * 8, 256, 0, st>>>((float *)lv[k], n, 0x9e3779b9u * (k + 1));
+    }
+}
+
 void launch_step_probe(const oed_ctx *ctx, int nsolve, int nrep, cudaStream_t st, cudaEvent_t ev0,
                        cudaEvent_t ev1)
 {
