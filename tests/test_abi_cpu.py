@@ -198,6 +198,20 @@ def test_workspace_holds_two_level_pairs_off_chip(P):
     assert 2 * n * 2 * b.nz * 416 * 4 < fb < 3 * n * 2 * b.nz * 416 * 4
 
 
+def test_workspace_holds_the_paired_layout(P):
+    """The two-step kernel keeps its levels in the paired layout: per row the even columns'
+    (x, z) pairs in sq slots, then the odd columns', sq = (nx + 1) / 2 + 4 rounded up to
+    even.  At 415 columns that is 848 floats a row against the planar 2 x 416, so the
+    workspace reserves the larger per solve."""
+    w = W.tiny(nx=415, nz=801, h=5.0, nsteps=50, nrec=4)
+    n = 30
+    sq = ((415 + 1) // 2 + 4 + 1) & ~1
+    paired_level = n * w.nz * 4 * sq * 4
+    assert 4 * sq > 2 * 416
+    f32 = P.oed_workspace_bytes(P.problem_from_workload(w, P.OED_FP32), n)
+    assert f32 >= 4 * paired_level
+
+
 def test_server_host_side_sizing_and_validation(P):
     """The server's footprint rule and submission checks run on the host: a request
     reserves a workspace for chunks of chunk_nodes nodes plus its arrays; a resume with
